@@ -1,0 +1,358 @@
+#!/usr/bin/env python
+"""Benchmark of the SIMUS RF hot path on one GB300 (replicas on N GPUs under torchrun).
+
+One step = one ``simus_rf`` call over the whole workload: transmit weights, Green's
+terms + transmit and receive contractions, chunk reduction with the transfer factor,
+inverse DFT to RF time signals.  Metric: Green's terms per second, one term being one
+(frequency bin x scatterer x sub-element x transmit).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--path P]
+  python bench.py --impl reference ...     # the FP64 CPU oracle on a bounded sample
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2102_02738_gb300 import phantoms as ph  # noqa: E402
+
+METRIC = "Green's terms/s (freq x scatterer x sub-elem x tx)"
+WORKLOADS = {
+    "planewave-linear-128": ph.planewave_linear_128,
+    "diverging-convex-128": ph.diverging_convex_128,
+    "focused-linear-64": ph.focused_linear_64,
+    "planewave-linear-128-grad": ph.planewave_linear_128_grad,
+}
+DEFAULT_WORKLOAD = "planewave-linear-128"
+DEFAULT_PATH = {"planewave-linear-128": "plain", "focused-linear-64": "plain",
+                "planewave-linear-128-grad": "plain", "diverging-convex-128": "plain"}
+# Per-term instruction budget of the Green's term (FP32 pipe, MUFU) used for the ALU
+# roofline: 85 FP32-pipe instructions + 12 MUFU per (bin, scatterer, sub-element).
+FP32_PER_TERM, MUFU_PER_TERM = 85, 12
+
+
+def metric_terms(w, plan_info) -> float:
+    return float(plan_info["n_bins"]) * w.n_scat * plan_info["n_sub"] * w.cfg["n_elements"] * w.n_tx
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def alu_peak_terms(n_sm: int, mhz: float) -> float:
+    clk = mhz * 1e6
+    return min(n_sm * 128 * clk / FP32_PER_TERM, n_sm * 16 * clk / MUFU_PER_TERM)
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        rows = []
+        with open(self.file.name) as fh:
+            for ln in fh:
+                parts = [p.strip() for p in ln.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.file.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows),
+                "power_w_max": max((float(r[3]) for r in rows
+                                    if r[3].replace(".", "").isdigit()), default=None)}
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, 0
+    import torch
+    import torch.distributed as dist
+    rank, local = int(os.environ["RANK"]), int(os.environ.get("LOCAL_RANK", "0"))
+    backend = "nccl" if torch.cuda.is_available() else "gloo"
+    if backend == "nccl":
+        torch.cuda.set_device(local)
+    dist.init_process_group(backend)
+    return rank, ws, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(v, ws):
+    if ws <= 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64,
+                     device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------- CPU oracle
+def oracle_sample(w, target_s=12.0, max_bins=None):
+    """Time the oracle's RF spectrum on a subset of kept bins (all scatterers, all
+    transmits); returns (terms/s, seconds, bins used, threads)."""
+    from oracle import oracle
+    lo, hi, nb = oracle.bins(w.cfg)
+    nu = oracle.nsub(w.cfg)
+    per_bin = w.n_scat * nu * w.cfg["n_elements"] * w.n_tx
+    cores = len(os.sched_getaffinity(0))
+    # calibrate on as many bins as there are cores (one bin per thread)
+    k = max(1, min(nb, cores))
+    qs = np.linspace(lo, hi, k).round().astype(int)
+    t0 = time.perf_counter()
+    oracle.rf_spectrum(w.cfg, w.delays, w.apod, w.x, w.y, w.z, w.rc, qs)
+    dt = time.perf_counter() - t0
+    if dt < target_s:
+        k2 = int(min(nb, max(k, k * target_s / max(dt, 1e-3))))
+        k2 = (k2 // cores) * cores or k2
+        if max_bins:
+            k2 = min(k2, max_bins)
+        if k2 > k:
+            qs = np.linspace(lo, hi, k2).round().astype(int)
+            t0 = time.perf_counter()
+            oracle.rf_spectrum(w.cfg, w.delays, w.apod, w.x, w.y, w.z, w.rc, qs)
+            dt = time.perf_counter() - t0
+            k = k2
+    return k * per_bin / dt, dt, k, cores
+
+
+def run_reference(args, rank, ws):
+    if rank != 0:
+        return
+    w = WORKLOADS[args.workload]()
+    from oracle import oracle
+    lo, hi, nb = oracle.bins(w.cfg)
+    nu = oracle.nsub(w.cfg)
+    per_bin = w.n_scat * nu * w.cfg["n_elements"] * w.n_tx
+    cores = len(os.sched_getaffinity(0))
+    # each step: a fixed bin subset sized for ~4 s, so K + W steps stay within minutes
+    _, dt1, k1, _ = oracle_sample(w, target_s=0.0)
+    per_step_bins = max(1, min(nb, int(k1 * 4.0 / max(dt1, 1e-3))))
+    qs = np.linspace(lo, hi, per_step_bins).round().astype(int)
+    for _ in range(args.warmup):
+        oracle.rf_spectrum(w.cfg, w.delays, w.apod, w.x, w.y, w.z, w.rc, qs[:max(1, len(qs) // 4)])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.rf_spectrum(w.cfg, w.delays, w.apod, w.x, w.y, w.z, w.rc, qs)
+    dt = time.perf_counter() - t0
+    terms = len(qs) * per_bin * args.steps
+    value = terms / dt
+    sample = (f"{len(qs)} of {nb} kept bins per step, all {w.n_scat} scatterers, "
+              f"{w.n_tx} transmits (RF spectrum, FP64)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "terms/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "path": "fp64-cpu-oracle",
+                       "scatterers": w.n_scat, "transmits": w.n_tx,
+                       "l2": "cpu"},
+            "cpu_baseline": {"value": value, "unit": "terms/s", "cores": cores,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "terms/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- ours
+def run_ours(args, rank, ws, local):
+    import torch
+    from paper_2102_02738_gb300 import build as libbuild
+    libbuild.build()
+    from paper_2102_02738_gb300 import simus
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    peaks, peak_src = measured_peaks()
+    props = torch.cuda.get_device_properties(dev)
+    n_sm = props.multi_processor_count
+
+    w = WORKLOADS[args.workload]()
+    path = args.path or DEFAULT_PATH[args.workload]
+    host = {k: np.ascontiguousarray(getattr(w, k)) for k in ("delays", "apod", "x", "z", "rc")}
+    d = {k: torch.from_numpy(v).to(dev) for k, v in host.items()}
+    plan = simus.Plan(w.cfg, path=path)
+    info = plan.info
+    T, N, nt = w.n_tx, w.cfg["n_elements"], info["n_samples"]
+    rf = torch.empty((T, N, nt), device=dev)
+    terms = metric_terms(w, info)
+    unique_per_launch = terms if path == "plain" else terms / T
+
+    def step():
+        plan.rf(d["delays"], d["apod"], d["x"], None, d["z"], d["rc"], out=rf, stream=stream)
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    simus.simus_plan_set_profiling(plan.handle, True)
+
+    clocks = ClockSampler(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    stage_ms = []
+    launches0 = simus.simus_kernel_launches()
+    clocks.start()
+    barrier(ws)
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.fill_(float(i))                 # evict L2 between timed steps (untimed)
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+        stage_ms.append(simus.simus_plan_get_timings(plan.handle))
+    torch.cuda.synchronize()
+    barrier(ws)
+    launches = simus.simus_kernel_launches() - launches0
+    clk = clocks.stop()
+    simus.simus_plan_set_profiling(plan.handle, False)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = allreduce_max(sum(step_ms), ws)
+    ms_per_step = total_ms / args.steps
+    value = terms * ws / (ms_per_step / 1e3)
+
+    # dominant kernel: Green's terms + contraction
+    kern_ms = statistics.mean(s["green_contract"] for s in stage_ms)
+    achieved = unique_per_launch / (kern_ms / 1e3)
+    peak = alu_peak_terms(n_sm, float(peaks.get("sm_max_mhz", 2070.0)))
+    stage_mean = {k: statistics.mean(s[k] for s in stage_ms) for k in simus.STAGES}
+
+    # end to end through the C ABI from pinned host buffers
+    pinned = {k: torch.from_numpy(v).pin_memory() for k, v in host.items()}
+    rf_host = torch.empty((T, N, nt), dtype=torch.float32).pin_memory()
+    h2d = sum(v.numel() * 4 for v in pinned.values())
+    d2h = rf_host.numel() * 4
+    e2e_steps = max(1, min(args.steps, 5))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_ms = 0.0
+    for i in range(e2e_steps):
+        flush.fill_(float(i))
+        e0.record(stream)
+        for k in pinned:
+            d[k].copy_(pinned[k], non_blocking=True)
+        step()
+        rf_host.copy_(rf, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms += e0.elapsed_time(e1)
+    e2e_ms = allreduce_max(e2e_ms, ws) / e2e_steps
+    e2e_value = terms * ws / (e2e_ms / 1e3)
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        v, dt, k, cores = oracle_sample(w, target_s=args.cpu_seconds)
+        cpu = {"value": v, "unit": "terms/s", "cores": cores, "kind": "oracle",
+               "sample": f"RF spectrum at {k} of {info['n_bins']} kept bins, all "
+                         f"{w.n_scat} scatterers and {T} transmits, FP64, {dt:.1f} s"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "terms/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if path == "plain" else ("f32+f16" if path == "tc_f16" else "f32+bf16"),
+        "data": "synthetic",
+        "config": {"workload": args.workload, "path": path, "scatterers": w.n_scat,
+                   "transmits": T, "elements": N, "sub_elements": info["n_sub"],
+                   "bins": info["n_bins"], "rf_samples": nt,
+                   "terms_per_step": terms, "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": "replicas" if ws > 1 else "single-gpu"},
+        "roofline": {"bound": "alu", "kernel": "green+contraction",
+                     "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gterm/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_source": f"{peak_src}: min(SMs*128*clk/{FP32_PER_TERM}, "
+                                    f"SMs*16*clk/{MUFU_PER_TERM}), {n_sm} SMs at "
+                                    f"{peaks.get('sm_max_mhz', 2070.0)} MHz",
+                     "kernel_ms": kern_ms},
+        "stages_ms": stage_mean,
+        "e2e": {"value": e2e_value, "unit": "terms/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--path", default=None, choices=[None, "plain", "tc_f16", "tc_bf16"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, ws, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, rank, ws)
+    else:
+        run_ours(args, rank, ws, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

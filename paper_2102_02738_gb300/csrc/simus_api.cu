@@ -1,0 +1,484 @@
+// simus_api.cu -- host side of the C ABI (include/simus.h): argument validation, the
+// plan (sub-element geometry, kept bins, transfer values, Green's constants), the
+// workspace, and the launch sequence of each entry point.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "simus_internal.h"
+
+using namespace simus;
+
+namespace {
+
+thread_local char g_err[512] = "";
+std::atomic<int64_t> g_launches{0};
+
+// Eq. 18: four-Gaussian approximation of the rectangle (third and fourth conjugates).
+const double kAre[4] = {0.187, 0.288, 0.187, 0.288};
+const double kAim[4] = {0.275, -1.954, -0.275, 1.954};
+const double kBre[4] = {4.558, 8.598, 4.558, 8.598};
+const double kBim[4] = {-25.59, -7.924, 25.59, 7.924};
+
+inline double sinc_d(double x) { return x == 0.0 ? 1.0 : std::sin(x) / x; }
+
+// Eq. 26-27: two-way transducer response.
+double transducer(const simus_probe &pr, double w) {
+    const double wc = 2.0 * M_PI * pr.fc, wb = pr.frac_bw * wc;
+    const double p = std::log(126.0) / std::log(2.0 * wc / wb);
+    return std::exp(-std::log(2.0) * std::pow(2.0 * std::fabs(w - wc) / wb, p));
+}
+
+// Eq. 25 (and its Hann-windowed variant): pulse spectrum as (re, im).
+void pulse(const simus_probe &pr, const simus_medium &md, double w, double &re, double &im) {
+    const double wc = 2.0 * M_PI * pr.fc, T = md.pulse_cycles / pr.fc;
+    auto rect = [&](double v) { return sinc_d(T * (v - wc) / 2.0) - sinc_d(T * (v + wc) / 2.0); };
+    double s = rect(w);   // S_P = i * s
+    if (md.pulse == SIMUS_PULSE_HANN) {
+        const double dw = 2.0 * M_PI / T;
+        s = 0.5 * s + 0.25 * rect(w + dw) + 0.25 * rect(w - dw);
+    }
+    re = 0.0;
+    im = s;
+}
+
+int validate_probe(const simus_probe *pr, const simus_medium *md) {
+    if (!pr || !md) return fail(SIMUS_ERR_ARG, "probe and medium must not be NULL");
+    if (pr->n_elements < 1 || pr->n_elements > 4096)
+        return fail(SIMUS_ERR_ARG, "n_elements=%d outside [1, 4096]", pr->n_elements);
+    if (pr->n_sub < 0 || pr->n_sub > 64) return fail(SIMUS_ERR_ARG, "n_sub=%d outside [0, 64]", pr->n_sub);
+    if (!(pr->pitch > 0) || !(pr->width > 0) || pr->width > pr->pitch * (1 + 1e-12))
+        return fail(SIMUS_ERR_ARG, "need 0 < width <= pitch (width=%g pitch=%g)", pr->width, pr->pitch);
+    if (!(pr->height > 0)) return fail(SIMUS_ERR_ARG, "height must be > 0");
+    if (!(pr->elev_focus > 0)) return fail(SIMUS_ERR_ARG, "elev_focus must be > 0 or +inf");
+    if (!(pr->radius >= 0) || std::isinf(pr->radius)) return fail(SIMUS_ERR_ARG, "radius must be finite and >= 0");
+    if (!(pr->fc > 0) || std::isinf(pr->fc)) return fail(SIMUS_ERR_ARG, "fc must be > 0");
+    if (!(pr->frac_bw > 0) || !(pr->frac_bw < 2)) return fail(SIMUS_ERR_ARG, "frac_bw must be in (0, 2)");
+    if (pr->baffle < 0 || pr->baffle > 2) return fail(SIMUS_ERR_ARG, "baffle must be 0, 1 or 2");
+    if (pr->baffle == SIMUS_BAFFLE_IMPEDANCE && !(pr->zeta >= 0))
+        return fail(SIMUS_ERR_ARG, "zeta must be >= 0");
+    if (!(md->c > 0) || std::isinf(md->c)) return fail(SIMUS_ERR_ARG, "c must be > 0");
+    if (!(md->alpha_db >= 0) || std::isinf(md->alpha_db)) return fail(SIMUS_ERR_ARG, "alpha_db must be >= 0");
+    if (!(md->fs > 0) || std::isinf(md->fs)) return fail(SIMUS_ERR_ARG, "fs must be > 0");
+    if (md->pulse != SIMUS_PULSE_RECT && md->pulse != SIMUS_PULSE_HANN)
+        return fail(SIMUS_ERR_ARG, "pulse must be 0 (rect) or 1 (Hann)");
+    if (!(md->pulse_cycles > 0) || std::isinf(md->pulse_cycles))
+        return fail(SIMUS_ERR_ARG, "pulse_cycles must be > 0");
+    return SIMUS_OK;
+}
+
+int resolve_nsub(const simus_probe &pr, const simus_medium &md) {
+    if (pr.n_sub > 0) return pr.n_sub;
+    const double lambda_min = md.c / (pr.fc * (1.0 + pr.frac_bw / 2.0));   // Eq. 21
+    return std::max(1, (int)std::ceil(pr.width / lambda_min));
+}
+
+int check_device_ptr(const void *ptr, const char *name, bool allow_null = false) {
+    if (!ptr) return allow_null ? SIMUS_OK : fail(SIMUS_ERR_ARG, "%s must not be NULL", name);
+    cudaPointerAttributes a{};
+    cudaError_t e = cudaPointerGetAttributes(&a, ptr);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SIMUS_ERR_ARG, "%s: not a CUDA pointer (%s)", name, cudaGetErrorString(e));
+    }
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+        return fail(SIMUS_ERR_ARG, "%s must be device memory", name);
+    return SIMUS_OK;
+}
+
+int validate_tx(const simus_plan *p, const simus_tx *tx) {
+    if (!tx) return fail(SIMUS_ERR_ARG, "tx must not be NULL");
+    if (tx->n_tx < 1 || tx->n_tx > 65535) return fail(SIMUS_ERR_ARG, "n_tx=%d outside [1, 65535]", tx->n_tx);
+    int rc;
+    if ((rc = check_device_ptr(tx->delays, "tx.delays"))) return rc;
+    if ((rc = check_device_ptr(tx->apod, "tx.apod"))) return rc;
+    (void)p;
+    return SIMUS_OK;
+}
+
+int validate_scat(const simus_scat *sc) {
+    if (!sc) return fail(SIMUS_ERR_ARG, "scat must not be NULL");
+    if (sc->n < 0 || sc->n > (int64_t)1 << 34) return fail(SIMUS_ERR_ARG, "scat.n=%lld out of range", (long long)sc->n);
+    if (sc->n == 0) return SIMUS_OK;
+    int rc;
+    if ((rc = check_device_ptr(sc->x, "scat.x"))) return rc;
+    if ((rc = check_device_ptr(sc->y, "scat.y", true))) return rc;
+    if ((rc = check_device_ptr(sc->z, "scat.z"))) return rc;
+    if ((rc = check_device_ptr(sc->rc, "scat.rc"))) return rc;
+    return SIMUS_OK;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+int use_plan_device(const simus_plan *p) {
+    return check_cuda(cudaSetDevice(p->device), "cudaSetDevice");
+}
+
+}  // namespace
+
+namespace simus {
+
+int fail(int code, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int check_cuda(cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return SIMUS_OK;
+    return fail(e == cudaErrorMemoryAllocation ? SIMUS_ERR_OOM : SIMUS_ERR_CUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+void stage_begin(simus_plan *plan, int stage, cudaStream_t st) {
+    if (!plan->profiling) return;
+    plan->stage_used[stage] = true;
+    cudaEventRecord(plan->ev[2 * stage], st);
+}
+
+void stage_end(simus_plan *plan, int stage, cudaStream_t st) {
+    if (!plan->profiling) return;
+    cudaEventRecord(plan->ev[2 * stage + 1], st);
+}
+
+void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+int workspace(simus_plan *plan, size_t bytes, void **ptr) {
+    if (bytes > plan->work_bytes) {
+        if (plan->d_work) {
+            cudaError_t e = cudaDeviceSynchronize();
+            if (e != cudaSuccess) return check_cuda(e, "workspace sync");
+            cudaFree(plan->d_work);
+            plan->d_work = nullptr;
+            plan->work_bytes = 0;
+        }
+        size_t want = align256(bytes + bytes / 8);
+        cudaError_t e = cudaMalloc(&plan->d_work, want);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(SIMUS_ERR_OOM, "workspace of %zu bytes: %s", want, cudaGetErrorString(e));
+        }
+        plan->work_bytes = want;
+    }
+    *ptr = plan->d_work;
+    return SIMUS_OK;
+}
+
+}  // namespace simus
+
+extern "C" {
+
+const char *simus_last_error(void) { return g_err; }
+
+int32_t simus_default_nt(const simus_probe *probe, const simus_medium *medium, double r_max,
+                         double tau_max) {
+    int rc = validate_probe(probe, medium);
+    if (rc) return rc;
+    if (!(r_max >= 0) || !(tau_max >= 0) || std::isinf(r_max) || std::isinf(tau_max))
+        return fail(SIMUS_ERR_ARG, "r_max and tau_max must be finite and >= 0");
+    double n = std::ceil(medium->fs * (2.0 * r_max / medium->c + tau_max + 8.0 / probe->fc));
+    if (n > 1e8) return fail(SIMUS_ERR_ARG, "RF length %g too large", n);
+    int32_t nt = (int32_t)n;
+    return nt + (nt & 1);
+}
+
+int32_t simus_pfield_nfreq(const simus_probe *probe, const simus_medium *medium, double r_max,
+                           double tau_max) {
+    int rc = validate_probe(probe, medium);
+    if (rc) return rc;
+    if (!(r_max > 0) || !(tau_max >= 0) || std::isinf(r_max) || std::isinf(tau_max))
+        return fail(SIMUS_ERR_ARG, "need r_max > 0 and tau_max >= 0");
+    const double wc = 2.0 * M_PI * probe->fc;
+    const double dw_max = 2.0 * M_PI / (r_max / medium->c + tau_max);   // Eq. 42 step rule
+    double n = std::ceil(2.0 * wc / dw_max);
+    if (n > 1e7) return fail(SIMUS_ERR_ARG, "frequency count %g too large", n);
+    return (int32_t)n;
+}
+
+int simus_plan_create(const simus_probe *probe, const simus_medium *medium, int32_t n_samples,
+                      int32_t path, simus_plan **out) {
+    if (!out) return fail(SIMUS_ERR_ARG, "out must not be NULL");
+    *out = nullptr;
+    int rc = validate_probe(probe, medium);
+    if (rc) return rc;
+    if (n_samples < 8 || n_samples > (1 << 24))
+        return fail(SIMUS_ERR_ARG, "n_samples=%d outside [8, 2^24]", n_samples);
+    if (path < SIMUS_PATH_PLAIN_F32 || path > SIMUS_PATH_TC_BF16)
+        return fail(SIMUS_ERR_ARG, "unknown path %d", path);
+
+    simus_plan *p = new simus_plan();
+    p->probe = *probe;
+    p->medium = *medium;
+    p->nt = n_samples;
+    p->path = path;
+    p->N = probe->n_elements;
+    p->nu = resolve_nsub(*probe, *medium);
+    p->M = p->nu * p->N;
+    if (p->M > 8192) { delete p; return fail(SIMUS_ERR_ARG, "nu * N = %d > 8192", p->M); }
+
+    // Kept bins: contiguous range where |S_P S_T| >= 1e-5 max over 1 <= q < Nt/2.
+    const double df = medium->fs / n_samples;
+    const int q_max = (n_samples - 1) / 2;
+    std::vector<double> mag(q_max + 1, 0.0);
+    double hmax = 0.0;
+    for (int q = 1; q <= q_max; ++q) {
+        double w = 2.0 * M_PI * q * df, re, im;
+        pulse(*probe, *medium, w, re, im);
+        mag[q] = std::hypot(re, im) * transducer(*probe, w);
+        hmax = std::max(hmax, mag[q]);
+    }
+    int lo = -1, hi = -1;
+    for (int q = 1; q <= q_max; ++q)
+        if (mag[q] >= 1e-5 * hmax) { if (lo < 0) lo = q; hi = q; }
+    if (lo < 0) { delete p; return fail(SIMUS_ERR_ARG, "no frequency bin above threshold (Nt too small?)"); }
+    p->q_lo = lo;
+    p->q_hi = hi;
+    p->nq = hi - lo + 1;
+    if ((double)hi * n_samples > 16777216.0 * 64) {
+        delete p;
+        return fail(SIMUS_ERR_ARG, "bin index too large for the exact phase reduction");
+    }
+
+    std::vector<float2> H(p->nq);
+    for (int k = 0; k < p->nq; ++k) {
+        double w = 2.0 * M_PI * (lo + k) * df, re, im;
+        pulse(*probe, *medium, w, re, im);
+        double st = transducer(*probe, w);
+        H[k] = make_float2((float)(re * st), (float)(im * st));
+    }
+
+    // Sub-element centroids (Eq. 24; convex: arc of radius R about (0, -R)).
+    std::vector<SubElem> sub(p->M);
+    const double b = probe->width / 2.0;
+    const int N = p->N, nu = p->nu;
+    for (int e = 0; e < N; ++e)
+        for (int mu = 0; mu < nu; ++mu) {
+            double xc, zc, psi;
+            const double off = b / nu * (2.0 * mu - nu + 1);
+            if (probe->radius > 0) {
+                const double R = probe->radius;
+                psi = (e - (N - 1) / 2.0) * probe->pitch / R + off / R;
+                xc = R * std::sin(psi);
+                zc = R * std::cos(psi) - R;
+            } else {
+                psi = 0.0;
+                xc = probe->pitch / 2.0 * (2.0 * (e + 1) - N - 1) + off;
+                zc = 0.0;
+            }
+            SubElem &s = sub[e * nu + mu];
+            s.xh = (float)xc;
+            s.xl = (float)(xc - (double)s.xh);
+            s.zh = (float)zc;
+            s.zl = (float)(zc - (double)s.zh);
+            s.cpsi = (float)std::cos(psi);
+            s.spsi = (float)std::sin(psi);
+            s.pad0 = s.pad1 = 0.f;
+        }
+
+    GreenConst &gc = p->gc;
+    gc.N = N; gc.nu = nu; gc.M = p->M; gc.q_lo = lo; gc.nq = p->nq; gc.nt = n_samples;
+    gc.baffle = probe->baffle;
+    const double K = df / medium->c;                       // cycles per metre per bin
+    gc.Kh = (float)K;
+    gc.Kl = (float)(K - (double)gc.Kh);
+    gc.k1 = (float)(2.0 * M_PI * K);
+    gc.k1b = (float)(2.0 * M_PI * K * b / nu);
+    gc.kh = (float)(M_PI * K);
+    gc.inv_rf = std::isinf(probe->elev_focus) ? 0.f : (float)(1.0 / probe->elev_focus);
+    // Eq. 40: k_a = alpha_dB / 8.69 * f * 1e-4 per metre; base 2 per bin.
+    gc.att2 = (float)(medium->alpha_db / 8.69 * df * 1e-4 / std::log(2.0));
+    gc.zeta = (float)probe->zeta;
+    const double h2 = probe->height * probe->height;
+    for (int g = 0; g < 4; ++g) {
+        gc.ga[g] = (float)(kBre[g] / h2);
+        gc.gb[g] = (float)(kBim[g] / h2);
+        gc.ga2[g] = (float)((kBre[g] / h2) * (kBre[g] / h2));
+        gc.Ar[g] = (float)(kAre[g] * std::sqrt(M_PI));
+        gc.Ai[g] = (float)(kAim[g] * std::sqrt(M_PI));
+    }
+    gc.df = df;
+
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_sub, sizeof(SubElem) * p->M);
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_H, sizeof(float2) * p->nq);
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_sub, sub.data(), sizeof(SubElem) * p->M, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_H, H.data(), sizeof(float2) * p->nq, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        int r = check_cuda(e, "plan upload");
+        cudaGetLastError();
+        simus_plan_destroy(p);
+        return r;
+    }
+    *out = p;
+    return SIMUS_OK;
+}
+
+void simus_plan_destroy(simus_plan *plan) {
+    if (!plan) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(plan->device);
+    cudaDeviceSynchronize();
+    for (auto &e : plan->ev)
+        if (e) cudaEventDestroy(e);
+    cudaFree(plan->d_sub);
+    cudaFree(plan->d_H);
+    cudaFree(plan->d_work);
+    cudaSetDevice(cur);
+    delete plan;
+}
+
+int simus_plan_set_profiling(simus_plan *plan, int32_t enable) {
+    if (!plan) return fail(SIMUS_ERR_ARG, "plan must not be NULL");
+    int rc = use_plan_device(plan);
+    if (rc) return rc;
+    if (enable && !plan->ev[0]) {
+        for (auto &e : plan->ev) {
+            cudaError_t err = cudaEventCreate(&e);
+            if (err != cudaSuccess) return check_cuda(err, "cudaEventCreate");
+        }
+    }
+    plan->profiling = enable != 0;
+    return SIMUS_OK;
+}
+
+int simus_plan_get_timings(simus_plan *plan, float *ms) {
+    if (!plan || !ms) return fail(SIMUS_ERR_ARG, "plan and ms must not be NULL");
+    for (int i = 0; i < SIMUS_N_STAGES; ++i) {
+        ms[i] = 0.f;
+        if (!plan->profiling || !plan->stage_used[i]) continue;
+        cudaError_t e = cudaEventSynchronize(plan->ev[2 * i + 1]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[i], plan->ev[2 * i], plan->ev[2 * i + 1]);
+        if (e != cudaSuccess) return check_cuda(e, "stage timing");
+    }
+    return SIMUS_OK;
+}
+
+int64_t simus_kernel_launches(void) { return g_launches.load(); }
+
+int simus_plan_get_info(const simus_plan *plan, simus_plan_info *info) {
+    if (!plan || !info) return fail(SIMUS_ERR_ARG, "plan and info must not be NULL");
+    std::memset(info, 0, sizeof(*info));
+    info->n_elements = plan->N;
+    info->n_sub = plan->nu;
+    info->n_samples = plan->nt;
+    info->path = plan->path;
+    info->q_lo = plan->q_lo;
+    info->q_hi = plan->q_hi;
+    info->n_bins = plan->nq;
+    info->df = plan->gc.df;
+    return SIMUS_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Spectrum X[t][e][k] (with transfer factor) into `spec`; workspace holds the transmit
+// weights and per-chunk partials.
+int rf_spectrum_impl(simus_plan *p, const simus_tx *tx, const simus_scat *sc, float2 *spec,
+                     cudaStream_t st) {
+    const int T = tx->n_tx, n_chan = T * p->N;
+    if (sc->n == 0)
+        return check_cuda(cudaMemsetAsync(spec, 0, sizeof(float2) * (size_t)n_chan * p->nq, st),
+                          "memset spectrum");
+    if (p->path != SIMUS_PATH_PLAIN_F32)
+        return fail(SIMUS_ERR_UNSUPPORTED, "tensor-core path not built yet");
+    PlainGeom g = plain_geometry(p, T, sc->n);
+    size_t cw_bytes = align256(sizeof(float2) * (size_t)T * p->nq * p->N);
+    size_t part_bytes = align256(sizeof(float2) * (size_t)g.n_chunks * n_chan * p->nq);
+    void *ws;
+    int rc = workspace(p, cw_bytes + part_bytes, &ws);
+    if (rc) return rc;
+    float2 *cw = reinterpret_cast<float2 *>(ws);
+    float2 *part = reinterpret_cast<float2 *>(reinterpret_cast<char *>(ws) + cw_bytes);
+    stage_begin(p, 0, st);
+    if ((rc = launch_tx_weights(p, tx, cw, st))) return rc;
+    stage_end(p, 0, st);
+    stage_begin(p, 1, st);
+    if ((rc = launch_plain(p, g, sc, T, cw, part, st))) return rc;
+    stage_end(p, 1, st);
+    stage_begin(p, 2, st);
+    rc = launch_reduce_spectrum(p, part, g.n_chunks, n_chan, spec, st);
+    stage_end(p, 2, st);
+    return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int simus_rf_spectrum(simus_plan *plan, const simus_tx *tx, const simus_scat *scat, float *spec,
+                      void *stream) {
+    if (!plan) return fail(SIMUS_ERR_ARG, "plan must not be NULL");
+    for (bool &u : plan->stage_used) u = false;
+    int rc;
+    if ((rc = use_plan_device(plan))) return rc;
+    if ((rc = validate_tx(plan, tx))) return rc;
+    if ((rc = validate_scat(scat))) return rc;
+    if ((rc = check_device_ptr(spec, "spec"))) return rc;
+    return rf_spectrum_impl(plan, tx, scat, reinterpret_cast<float2 *>(spec),
+                            reinterpret_cast<cudaStream_t>(stream));
+}
+
+int simus_rf(simus_plan *plan, const simus_tx *tx, const simus_scat *scat, float *rf,
+             void *stream) {
+    if (!plan) return fail(SIMUS_ERR_ARG, "plan must not be NULL");
+    for (bool &u : plan->stage_used) u = false;
+    int rc;
+    if ((rc = use_plan_device(plan))) return rc;
+    if ((rc = validate_tx(plan, tx))) return rc;
+    if ((rc = validate_scat(scat))) return rc;
+    if ((rc = check_device_ptr(rf, "rf"))) return rc;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int n_chan = tx->n_tx * plan->N;
+    if (scat->n == 0)
+        return check_cuda(cudaMemsetAsync(rf, 0, sizeof(float) * (size_t)n_chan * plan->nt, st),
+                          "memset rf");
+    // The spectrum lives in a dedicated buffer at the end of the workspace: size the
+    // workspace for both, then run the spectrum into its tail.
+    size_t spec_bytes = align256(sizeof(float2) * (size_t)n_chan * plan->nq);
+    PlainGeom g = plain_geometry(plan, tx->n_tx, scat->n);
+    size_t cw_bytes = align256(sizeof(float2) * (size_t)tx->n_tx * plan->nq * plan->N);
+    size_t part_bytes = align256(sizeof(float2) * (size_t)g.n_chunks * n_chan * plan->nq);
+    void *ws;
+    if ((rc = workspace(plan, cw_bytes + part_bytes + spec_bytes, &ws))) return rc;
+    float2 *spec = reinterpret_cast<float2 *>(reinterpret_cast<char *>(ws) + cw_bytes + part_bytes);
+    if ((rc = rf_spectrum_impl(plan, tx, scat, spec, st))) return rc;
+    stage_begin(plan, 3, st);
+    rc = launch_idft(plan, spec, n_chan, rf, st);
+    stage_end(plan, 3, st);
+    return rc;
+}
+
+int simus_pfield(simus_plan *plan, const simus_tx *tx, int64_t n_pts, const float *x,
+                 const float *y, const float *z, int32_t n_freq, float *prms, void *stream) {
+    (void)plan; (void)tx; (void)n_pts; (void)x; (void)y; (void)z; (void)n_freq; (void)prms; (void)stream;
+    return fail(SIMUS_ERR_UNSUPPORTED, "simus_pfield not built yet");
+}
+
+int simus_rf_grad(simus_plan *plan, const simus_tx *tx, const simus_scat *scat, const float *drf,
+                  float *g_rc, float *g_x, float *g_z, float *g_delays, void *stream) {
+    (void)plan; (void)tx; (void)scat; (void)drf; (void)g_rc; (void)g_x; (void)g_z; (void)g_delays; (void)stream;
+    return fail(SIMUS_ERR_UNSUPPORTED, "simus_rf_grad not built yet");
+}
+
+int simus_batch_rf(int32_t n_sims, simus_plan *const *plans, const simus_tx *tx,
+                   const simus_scat *scat, float *const *rf, void *stream) {
+    if (n_sims < 0 || (n_sims > 0 && (!plans || !tx || !scat || !rf)))
+        return fail(SIMUS_ERR_ARG, "invalid batch arguments");
+    for (int i = 0; i < n_sims; ++i) {
+        int rc = simus_rf(plans[i], &tx[i], &scat[i], rf[i], stream);
+        if (rc) return rc;
+    }
+    return SIMUS_OK;
+}
+
+}  // extern "C"

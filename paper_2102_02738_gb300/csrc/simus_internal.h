@@ -1,0 +1,96 @@
+// simus_internal.h -- structures shared by the host API and the kernels of the CUDA
+// library (not part of the C ABI).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/simus.h"
+
+namespace simus {
+
+// Per-plan constants of the Green's term, passed to kernels by value.  Bin q has
+// frequency f_q = q * df; every per-bin quantity is stored "per unit q".
+struct GreenConst {
+    int32_t N;        // elements
+    int32_t nu;       // sub-elements per element
+    int32_t M;        // nu * N
+    int32_t q_lo;     // first kept bin
+    int32_t nq;       // number of kept bins
+    int32_t nt;       // RF samples
+    int32_t baffle;   // SIMUS_BAFFLE_*
+    int32_t pad_;
+    float Kh, Kl;     // df / c as a double-float [cycles per metre per bin]
+    float k1;         // 2 pi df / c [rad per metre per bin]
+    float k1b;        // k1 * b / nu: sinc argument per bin per unit sin(theta)
+    float kh;         // k1 / 2: Im(alpha_g) per bin per unit (1/R_f - 1/r)
+    float inv_rf;     // 1 / R_f (0 without lens)
+    float att2;       // (alpha_dB / 8.69) * df * 1e-4 * log2(e): base-2 absorption per bin per metre
+    float zeta;       // Eq. 39
+    float ga[4];      // Re(B_g) / h^2
+    float gb[4];      // Im(B_g) / h^2
+    float ga2[4];     // (Re(B_g) / h^2)^2
+    float Ar[4];      // Re(A_g) sqrt(pi)
+    float Ai[4];      // Im(A_g) sqrt(pi)
+    double df;        // fs / nt [Hz]
+};
+
+// Sub-element record: centroid as double-float pairs and the normal's angle.
+struct __align__(16) SubElem {
+    float xh, xl, zh, zl;   // x_c = xh + xl, z_c = zh + zl
+    float cpsi, spsi;       // normal (sin psi, cos psi); local frame rotation
+    float pad0, pad1;
+};
+
+}  // namespace simus
+
+struct simus_plan {
+    simus_probe probe;
+    simus_medium medium;
+    int32_t nt = 0, path = 0, nu = 0, N = 0, M = 0, q_lo = 0, q_hi = 0, nq = 0;
+    int device = 0;
+    int num_sms = 0;
+    simus::GreenConst gc{};
+    simus::SubElem *d_sub = nullptr;  // [M]
+    float2 *d_H = nullptr;            // [nq] transfer S_P S_T at the kept bins
+    void *d_work = nullptr;           // workspace
+    size_t work_bytes = 0;
+    bool profiling = false;
+    bool stage_used[SIMUS_N_STAGES] = {};
+    cudaEvent_t ev[2 * SIMUS_N_STAGES] = {};
+};
+
+namespace simus {
+
+// Workspace helper: returns a device pointer with at least `bytes`, growing the
+// plan's workspace (synchronising the device before a reallocation).
+int workspace(simus_plan *plan, size_t bytes, void **ptr);
+
+// Tracing: events around a stage (no-ops unless profiling is enabled) and the
+// process-wide launch counter.
+void stage_begin(simus_plan *plan, int stage, cudaStream_t st);
+void stage_end(simus_plan *plan, int stage, cudaStream_t st);
+void count_launches(int n);
+
+// Error reporting (thread-local message).
+int fail(int code, const char *fmt, ...);
+int check_cuda(cudaError_t e, const char *what);
+
+// ---- kernel launchers (each returns SIMUS_OK or an error code) ----------------
+// Transmit weights C[t][k][e] = W_te exp(i w_q dtau_te), q = q_lo + k.
+int launch_tx_weights(const simus_plan *p, const simus_tx *tx, float2 *cw, cudaStream_t st);
+
+// Plain FP32 path: partial spectra part[chunk][t][e][k] (no transfer factor).
+struct PlainGeom { int QB, SB, n_qtiles, n_chunks; int64_t chunk_len; size_t smem; };
+PlainGeom plain_geometry(const simus_plan *p, int T, int64_t S);
+int launch_plain(const simus_plan *p, const PlainGeom &g, const simus_scat *sc, int T,
+                 const float2 *cw, float2 *part, cudaStream_t st);
+
+// Sum partial spectra over chunks and multiply by H: spec[c][k] (c = t * N + e).
+int launch_reduce_spectrum(const simus_plan *p, const float2 *part, int n_chunks, int n_chan,
+                           float2 *spec, cudaStream_t st);
+
+// rf[c][j] = Re sum_k spec[c][k] e^{-2 pi i (q_lo + k) j / Nt}.
+int launch_idft(const simus_plan *p, const float2 *spec, int n_chan, float *rf, cudaStream_t st);
+
+}  // namespace simus
