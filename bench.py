@@ -180,9 +180,9 @@ def run_reference(args, rank, ws):
     nu = oracle.nsub(w.cfg)
     per_bin = w.n_scat * nu * w.cfg["n_elements"] * w.n_tx
     cores = len(os.sched_getaffinity(0))
-    # each step: a fixed bin subset sized for ~4 s, so K + W steps stay within minutes
+    # each step: a fixed bin subset sized for ~3 s, so K + W steps stay within minutes
     _, dt1, k1, _ = oracle_sample(w, target_s=0.0)
-    per_step_bins = max(1, min(nb, int(k1 * 4.0 / max(dt1, 1e-3))))
+    per_step_bins = max(1, min(nb, int(k1 * 3.0 / max(dt1, 1e-3))))
     qs = np.linspace(lo, hi, per_step_bins).round().astype(int)
     for _ in range(args.warmup):
         oracle.rf_spectrum(w.cfg, w.delays, w.apod, w.x, w.y, w.z, w.rc, qs[:max(1, len(qs) // 4)])
@@ -223,7 +223,7 @@ def run_ours(args, rank, ws, local):
     props = torch.cuda.get_device_properties(dev)
     n_sm = props.multi_processor_count
 
-    w = WORKLOADS[args.workload]()
+    w = WORKLOADS[args.workload](**({"n_scat": args.n_scat} if args.n_scat else {}))
     path = args.path or DEFAULT_PATH[args.workload]
     host = {k: np.ascontiguousarray(getattr(w, k)) for k in ("delays", "apod", "x", "z", "rc")}
     d = {k: torch.from_numpy(v).to(dev) for k, v in host.items()}
@@ -249,6 +249,7 @@ def run_ours(args, rank, ws, local):
     stage_ms = []
     launches0 = simus.simus_kernel_launches()
     clocks.start()
+    time.sleep(0.5)                             # let the sampler come up
     barrier(ws)
     torch.cuda.synchronize()
     for i in range(args.steps):
@@ -336,13 +337,15 @@ def run_ours(args, rank, ws, local):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--path", default=None, choices=[None, "plain", "tc_f16", "tc_bf16"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n-scat", type=int, default=0,
+                    help="override the workload's scatterer count (profiling of small cases)")
     args = ap.parse_args()
     rank, ws, local = dist_init()
     if args.impl == "reference":

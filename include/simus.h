@@ -188,6 +188,12 @@ int simus_rf_grad(simus_plan *plan, const simus_tx *tx, const simus_scat *scat,
 int simus_batch_rf(int32_t n_sims, simus_plan *const *plans, const simus_tx *tx,
                    const simus_scat *scat, float *const *rf, void *stream);
 
+/* Wait for all work queued on the plan's device, then report a failure that an earlier
+ * asynchronous call on this plan met on the device: SIMUS_ERR_TIMEOUT if a bounded wait
+ * inside a kernel gave up (that call's outputs are invalid; the flag is then cleared),
+ * SIMUS_ERR_CUDA for an asynchronous CUDA error, else SIMUS_OK. */
+int simus_plan_check(simus_plan *plan);
+
 /* Per-stage timing of the calls made on a plan (tracing).  With profiling enabled,
  * each entry point records CUDA events around its kernels on the call's stream;
  * simus_plan_get_timings waits for them and writes the durations in milliseconds of

@@ -52,7 +52,7 @@ int launch_tx_weights(const simus_plan *p, const simus_tx *tx, float2 *cw, cudaS
     return check_cuda(cudaGetLastError(), "k_tx_weights launch");
 }
 
-template <int QB, bool HAS_Y>
+template <int QB, bool HAS_Y, bool NARROW>
 __global__ void __launch_bounds__(kPlainThreads, 2)
 k_plain_rf(const GreenConst gc, const SubElem *__restrict__ sub_g, const float *__restrict__ xg,
            const float *__restrict__ yg, const float *__restrict__ zg,
@@ -99,13 +99,18 @@ k_plain_rf(const GreenConst gc, const SubElem *__restrict__ sub_g, const float *
             for (int j = 0; j < QB; ++j) G[j] = make_float2(0.f, 0.f);
             for (int mu = 0; mu < nu; ++mu) {
                 PairSetup P = pair_setup<HAS_Y>(gc, sub[e * nu + mu], ps.x, ps.y, ps.z, q0);
-                float amp = P.amp0;
+                PhaseRun R = phase_run(P, q0);
 #pragma unroll
                 for (int j = 0; j < QB; ++j) {
-                    float2 g = green_term<HAS_Y>(gc, P, q0 + (float)j, amp);
-                    G[j].x += g.x;
-                    G[j].y += g.y;
-                    amp *= P.mstep;
+                    const float q = q0 + (float)j;
+                    const float m = sinc_f<NARROW>(q * P.xb);
+                    const float2 d = delta_f<HAS_Y>(gc, P, q);
+                    const float er = R.zr * m, ei = R.zi * m;
+                    G[j].x = fmaf(er, d.x, fmaf(-ei, d.y, G[j].x));
+                    G[j].y = fmaf(er, d.y, fmaf(ei, d.x, G[j].y));
+                    const float nzr = fmaf(R.zr, R.wr, -R.zi * R.wi);
+                    R.zi = fmaf(R.zr, R.wi, R.zi * R.wr);
+                    R.zr = nzr;
                 }
             }
 #pragma unroll
@@ -187,8 +192,9 @@ PlainGeom plain_geometry(const simus_plan *p, int T, int64_t S) {
 int launch_plain(const simus_plan *p, const PlainGeom &g, const simus_scat *sc, int T,
                  const float2 *cw, float2 *part, cudaStream_t st) {
     dim3 grid(g.n_qtiles, g.n_chunks, T);
-    bool has_y = sc->y != nullptr;
-    auto kern = has_y ? k_plain_rf<kPlainQB, true> : k_plain_rf<kPlainQB, false>;
+    const bool has_y = sc->y != nullptr, narrow = p->gc.narrow != 0;
+    auto kern = has_y ? (narrow ? k_plain_rf<kPlainQB, true, true> : k_plain_rf<kPlainQB, true, false>)
+                      : (narrow ? k_plain_rf<kPlainQB, false, true> : k_plain_rf<kPlainQB, false, false>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)g.smem);
     if (e != cudaSuccess) return check_cuda(e, "k_plain_rf smem attribute");

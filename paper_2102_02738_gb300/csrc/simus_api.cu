@@ -299,15 +299,18 @@ int simus_plan_create(const simus_probe *probe, const simus_medium *medium, int3
         gc.ga[g] = (float)(kBre[g] / h2);
         gc.gb[g] = (float)(kBim[g] / h2);
         gc.ga2[g] = (float)((kBre[g] / h2) * (kBre[g] / h2));
-        gc.Ar[g] = (float)(kAre[g] * std::sqrt(M_PI));
-        gc.Ai[g] = (float)(kAim[g] * std::sqrt(M_PI));
+        gc.Cr[g] = (float)(kAre[g] * std::sqrt(M_PI / 2.0));
+        gc.Ci[g] = (float)(kAim[g] * std::sqrt(M_PI / 2.0));
     }
+    gc.narrow = (2.0 * M_PI * K * b / nu) * hi <= 3.19 ? 1 : 0;
     gc.df = df;
 
     cudaError_t e = cudaGetDevice(&p->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
     if (e == cudaSuccess) e = cudaMalloc(&p->d_sub, sizeof(SubElem) * p->M);
     if (e == cudaSuccess) e = cudaMalloc(&p->d_H, sizeof(float2) * p->nq);
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(p->d_err, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemcpy(p->d_sub, sub.data(), sizeof(SubElem) * p->M, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(p->d_H, H.data(), sizeof(float2) * p->nq, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
@@ -330,9 +333,26 @@ void simus_plan_destroy(simus_plan *plan) {
         if (e) cudaEventDestroy(e);
     cudaFree(plan->d_sub);
     cudaFree(plan->d_H);
+    cudaFree(plan->d_err);
     cudaFree(plan->d_work);
     cudaSetDevice(cur);
     delete plan;
+}
+
+int simus_plan_check(simus_plan *plan) {
+    if (!plan) return fail(SIMUS_ERR_ARG, "plan must not be NULL");
+    int rc = use_plan_device(plan);
+    if (rc) return rc;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return check_cuda(e, "asynchronous error");
+    int flag = 0;
+    e = cudaMemcpy(&flag, plan->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return check_cuda(e, "reading the device error flag");
+    if (flag) {
+        cudaMemset(plan->d_err, 0, sizeof(int));
+        return fail(SIMUS_ERR_TIMEOUT, "a bounded device wait gave up (code %d); outputs invalid", flag);
+    }
+    return SIMUS_OK;
 }
 
 int simus_plan_set_profiling(simus_plan *plan, int32_t enable) {
@@ -381,32 +401,60 @@ int simus_plan_get_info(const simus_plan *plan, simus_plan_info *info) {
 
 namespace {
 
-// Spectrum X[t][e][k] (with transfer factor) into `spec`; workspace holds the transmit
-// weights and per-chunk partials.
-int rf_spectrum_impl(simus_plan *p, const simus_tx *tx, const simus_scat *sc, float2 *spec,
-                     cudaStream_t st) {
+// Workspace layout of one RF call: [weights | partial spectra | spectrum (simus_rf)].
+struct CallLayout {
+    bool tc;
+    PlainGeom pg;
+    TcGeom tg;
+    int n_chunks;
+    size_t w_bytes, part_bytes, spec_bytes;
+    size_t total() const { return w_bytes + part_bytes + spec_bytes; }
+};
+
+int call_layout(const simus_plan *p, int T, int64_t S, bool with_spec, CallLayout &L) {
+    const int n_chan = T * p->N;
+    L = CallLayout{};
+    L.tc = p->path != SIMUS_PATH_PLAIN_F32;
+    if (L.tc) {
+        L.tg = tc_geometry(p, T, S);
+        if (!L.tg.ok)
+            return fail(SIMUS_ERR_UNSUPPORTED,
+                        "tensor-core path needs N <= 128 and 2T <= 256 (N=%d, T=%d)", p->N, T);
+        L.n_chunks = L.tg.n_chunks;
+        L.w_bytes = align256(L.tg.b1_bytes);
+    } else {
+        L.pg = plain_geometry(p, T, S);
+        L.n_chunks = L.pg.n_chunks;
+        L.w_bytes = align256(sizeof(float2) * (size_t)T * p->nq * p->N);
+    }
+    L.part_bytes = align256(sizeof(float2) * (size_t)L.n_chunks * n_chan * p->nq);
+    L.spec_bytes = with_spec ? align256(sizeof(float2) * (size_t)n_chan * p->nq) : 0;
+    return SIMUS_OK;
+}
+
+// Spectrum X[t][e][k] (with transfer factor) into `spec`, workspace per `L` at `ws`.
+int rf_spectrum_run(simus_plan *p, const CallLayout &L, void *ws, const simus_tx *tx,
+                    const simus_scat *sc, float2 *spec, cudaStream_t st) {
     const int T = tx->n_tx, n_chan = T * p->N;
-    if (sc->n == 0)
-        return check_cuda(cudaMemsetAsync(spec, 0, sizeof(float2) * (size_t)n_chan * p->nq, st),
-                          "memset spectrum");
-    if (p->path != SIMUS_PATH_PLAIN_F32)
-        return fail(SIMUS_ERR_UNSUPPORTED, "tensor-core path not built yet");
-    PlainGeom g = plain_geometry(p, T, sc->n);
-    size_t cw_bytes = align256(sizeof(float2) * (size_t)T * p->nq * p->N);
-    size_t part_bytes = align256(sizeof(float2) * (size_t)g.n_chunks * n_chan * p->nq);
-    void *ws;
-    int rc = workspace(p, cw_bytes + part_bytes, &ws);
-    if (rc) return rc;
-    float2 *cw = reinterpret_cast<float2 *>(ws);
-    float2 *part = reinterpret_cast<float2 *>(reinterpret_cast<char *>(ws) + cw_bytes);
-    stage_begin(p, 0, st);
-    if ((rc = launch_tx_weights(p, tx, cw, st))) return rc;
-    stage_end(p, 0, st);
-    stage_begin(p, 1, st);
-    if ((rc = launch_plain(p, g, sc, T, cw, part, st))) return rc;
-    stage_end(p, 1, st);
+    char *base = reinterpret_cast<char *>(ws);
+    float2 *part = reinterpret_cast<float2 *>(base + L.w_bytes);
+    int rc;
+    if (L.tc) {
+        stage_begin(p, 1, st);
+        rc = launch_tc(p, L.tg, tx, sc, reinterpret_cast<uint16_t *>(base), part, p->d_err, st);
+        stage_end(p, 1, st);
+        if (rc) return rc;
+    } else {
+        float2 *cw = reinterpret_cast<float2 *>(base);
+        stage_begin(p, 0, st);
+        if ((rc = launch_tx_weights(p, tx, cw, st))) return rc;
+        stage_end(p, 0, st);
+        stage_begin(p, 1, st);
+        if ((rc = launch_plain(p, L.pg, sc, T, cw, part, st))) return rc;
+        stage_end(p, 1, st);
+    }
     stage_begin(p, 2, st);
-    rc = launch_reduce_spectrum(p, part, g.n_chunks, n_chan, spec, st);
+    rc = launch_reduce_spectrum(p, part, L.n_chunks, n_chan, spec, st);
     stage_end(p, 2, st);
     return rc;
 }
@@ -424,8 +472,15 @@ int simus_rf_spectrum(simus_plan *plan, const simus_tx *tx, const simus_scat *sc
     if ((rc = validate_tx(plan, tx))) return rc;
     if ((rc = validate_scat(scat))) return rc;
     if ((rc = check_device_ptr(spec, "spec"))) return rc;
-    return rf_spectrum_impl(plan, tx, scat, reinterpret_cast<float2 *>(spec),
-                            reinterpret_cast<cudaStream_t>(stream));
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (scat->n == 0)
+        return check_cuda(cudaMemsetAsync(spec, 0, sizeof(float2) * (size_t)tx->n_tx * plan->N * plan->nq, st),
+                          "memset spectrum");
+    CallLayout L;
+    if ((rc = call_layout(plan, tx->n_tx, scat->n, false, L))) return rc;
+    void *ws;
+    if ((rc = workspace(plan, L.total(), &ws))) return rc;
+    return rf_spectrum_run(plan, L, ws, tx, scat, reinterpret_cast<float2 *>(spec), st);
 }
 
 int simus_rf(simus_plan *plan, const simus_tx *tx, const simus_scat *scat, float *rf,
@@ -442,16 +497,12 @@ int simus_rf(simus_plan *plan, const simus_tx *tx, const simus_scat *scat, float
     if (scat->n == 0)
         return check_cuda(cudaMemsetAsync(rf, 0, sizeof(float) * (size_t)n_chan * plan->nt, st),
                           "memset rf");
-    // The spectrum lives in a dedicated buffer at the end of the workspace: size the
-    // workspace for both, then run the spectrum into its tail.
-    size_t spec_bytes = align256(sizeof(float2) * (size_t)n_chan * plan->nq);
-    PlainGeom g = plain_geometry(plan, tx->n_tx, scat->n);
-    size_t cw_bytes = align256(sizeof(float2) * (size_t)tx->n_tx * plan->nq * plan->N);
-    size_t part_bytes = align256(sizeof(float2) * (size_t)g.n_chunks * n_chan * plan->nq);
+    CallLayout L;
+    if ((rc = call_layout(plan, tx->n_tx, scat->n, true, L))) return rc;
     void *ws;
-    if ((rc = workspace(plan, cw_bytes + part_bytes + spec_bytes, &ws))) return rc;
-    float2 *spec = reinterpret_cast<float2 *>(reinterpret_cast<char *>(ws) + cw_bytes + part_bytes);
-    if ((rc = rf_spectrum_impl(plan, tx, scat, spec, st))) return rc;
+    if ((rc = workspace(plan, L.total(), &ws))) return rc;
+    float2 *spec = reinterpret_cast<float2 *>(reinterpret_cast<char *>(ws) + L.w_bytes + L.part_bytes);
+    if ((rc = rf_spectrum_run(plan, L, ws, tx, scat, spec, st))) return rc;
     stage_begin(plan, 3, st);
     rc = launch_idft(plan, spec, n_chan, rf, st);
     stage_end(plan, 3, st);

@@ -30,8 +30,10 @@ struct GreenConst {
     float ga[4];      // Re(B_g) / h^2
     float gb[4];      // Im(B_g) / h^2
     float ga2[4];     // (Re(B_g) / h^2)^2
-    float Ar[4];      // Re(A_g) sqrt(pi)
-    float Ai[4];      // Im(A_g) sqrt(pi)
+    float Cr[4];      // Re(A_g) sqrt(pi / 2)
+    float Ci[4];      // Im(A_g) sqrt(pi / 2)
+    int32_t narrow;   // 1 if |k b / nu| <= 3.2 at every kept bin (polynomial sinc suffices)
+    int32_t pad2_;
     double df;        // fs / nt [Hz]
 };
 
@@ -53,6 +55,7 @@ struct simus_plan {
     simus::GreenConst gc{};
     simus::SubElem *d_sub = nullptr;  // [M]
     float2 *d_H = nullptr;            // [nq] transfer S_P S_T at the kept bins
+    int *d_err = nullptr;             // device-side error flag (bounded waits)
     void *d_work = nullptr;           // workspace
     size_t work_bytes = 0;
     bool profiling = false;
@@ -85,6 +88,17 @@ struct PlainGeom { int QB, SB, n_qtiles, n_chunks; int64_t chunk_len; size_t sme
 PlainGeom plain_geometry(const simus_plan *p, int T, int64_t S);
 int launch_plain(const simus_plan *p, const PlainGeom &g, const simus_scat *sc, int T,
                  const float2 *cw, float2 *part, cudaStream_t st);
+
+// Batched tensor-core path (FP16 / BF16 operands, FP32 accumulation).
+struct TcGeom {
+    bool ok;             // the problem fits this kernel (N <= 128, 2T <= 256, smem)
+    int Np, nN, QB;      // padded elements, padded GEMM N (2T), bins per work item
+    int n_btiles, n_chunks, tiles_per_chunk, n_items, grid;
+    size_t smem, b1_bytes;
+};
+TcGeom tc_geometry(const simus_plan *p, int T, int64_t S);
+int launch_tc(const simus_plan *p, const TcGeom &g, const simus_tx *tx, const simus_scat *sc,
+              uint16_t *b1img, float2 *part, int *err, cudaStream_t st);
 
 // Sum partial spectra over chunks and multiply by H: spec[c][k] (c = t * N + e).
 int launch_reduce_spectrum(const simus_plan *p, const float2 *part, int n_chunks, int n_chan,

@@ -1,0 +1,97 @@
+"""Parity of the batched tensor-core path (FP16 / BF16 operands on tcgen05, FP32
+accumulation) with the FP64 oracle, through the C ABI.
+
+Tolerance: relative L2 error <= 2e-3 over the compared outputs (the accuracy target of
+the reduced-precision contraction); the FP32 Green's-term generation is shared with the
+plain path, whose own tolerance is 1e-5.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2102_02738_gb300 import phantoms as ph
+
+pytestmark = pytest.mark.gpu
+TOL_TC = 2e-3
+
+
+@pytest.fixture(scope="module")
+def S():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2102_02738_gb300 import build
+    build.build()
+    from paper_2102_02738_gb300 import simus
+    return simus
+
+
+def dev(a):
+    return None if a is None else torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+
+
+def run(S, w, path, spectrum=False):
+    plan = S.Plan(w.cfg, path=path)
+    args = [dev(a) for a in (w.delays, w.apod, w.x, w.y, w.z, w.rc)]
+    out = plan.rf_spectrum(*args) if spectrum else plan.rf(*args)
+    S.lib.simus_plan_check(plan.handle) == 0 or pytest.fail(S.lib.simus_last_error().decode())
+    out = out.cpu().numpy()
+    info = plan.info
+    plan.close()
+    return out, info
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+@pytest.mark.parametrize("kw", [
+    dict(),
+    dict(n_elements=16, n_scat=300, n_tx=5),                 # several scatterer tiles
+    dict(n_elements=13, n_sub=3, n_scat=150, n_tx=3),        # N not a multiple of 8
+    dict(convex=True, n_elements=24, n_scat=200, n_tx=9),
+    dict(y_spread=1e-3, n_scat=130),
+])
+def test_tc_f16_rf_tiny(S, oracle, kw):
+    w = ph.tiny(**kw)
+    ref = oracle.rf(w.cfg, w.delays, w.apod, w.x, w.y, w.z, w.rc)
+    got, _ = run(S, w, "tc_f16")
+    assert rel_l2(got, ref) <= TOL_TC
+
+
+def test_tc_f16_matches_plain_spectrum(S):
+    """Same Green's terms, different contraction precision: the two GPU paths agree to
+    the FP16 budget on a case with many bin tiles and scatterer tiles."""
+    w = ph.tiny(n_elements=64, n_sub=2, n_scat=1000, n_tx=12, nt=900)
+    a, _ = run(S, w, "plain", spectrum=True)
+    b, _ = run(S, w, "tc_f16", spectrum=True)
+    assert rel_l2(b, a) <= TOL_TC
+
+
+def test_tc_bf16_error_is_reported(S, oracle):
+    """BF16 operands (8-bit mantissa): the error is measured and bounded."""
+    w = ph.tiny(n_elements=32, n_scat=400, n_tx=7)
+    ref = oracle.rf(w.cfg, w.delays, w.apod, w.x, w.y, w.z, w.rc)
+    got, _ = run(S, w, "tc_bf16")
+    err = rel_l2(got, ref)
+    print(f"bf16 rel-L2 {err:.3e}")
+    assert err <= 2e-2
+
+
+def test_tc_diverging_convex_128_sampled_bins(S, oracle):
+    """Full-size 128-element convex array, 31 diverging waves, 100,000 scatterers, in the
+    launch configuration the benchmark times: spectra at sampled bins vs the oracle."""
+    w = ph.diverging_convex_128()
+    got, info = run(S, w, "tc_f16", spectrum=True)
+    lo = info["q_lo"]
+    ks = np.array([3, info["n_bins"] // 2, info["n_bins"] - 2])
+    ref = oracle.rf_spectrum(w.cfg, w.delays, w.apod, w.x, w.y, w.z, w.rc, lo + ks)
+    assert rel_l2(got[..., ks], ref) <= TOL_TC
+
+
+def test_tc_linearity(S):
+    w = ph.tiny(n_elements=32, n_scat=500, n_tx=4)
+    a, _ = run(S, w, "tc_f16")
+    w.rc = (2.0 * w.rc).astype(np.float32)
+    b, _ = run(S, w, "tc_f16")
+    # FP16 rounding of 2 R P equals 2 x the rounding of R P (power-of-two scale)
+    np.testing.assert_allclose(b, 2.0 * a, rtol=0, atol=1e-6 * np.abs(a).max())
