@@ -208,6 +208,28 @@ int simus_plan_get_timings(simus_plan *plan, float *ms);
 /* Number of kernels this library has launched in the process so far (tracing). */
 int64_t simus_kernel_launches(void);
 
+/* ---- Allocation-free RF (the paper has no counterpart; an interface for callers) -----
+ * simus_rf_noalloc computes what simus_rf computes on a SIMUS_PATH_PLAIN_F32 plan built
+ * from the same probe, medium and n_samples, without allocating device memory.  It is
+ * for callers that cannot allocate: code running under a stream capture in global
+ * capture mode (where cudaMalloc is refused), latency-critical loops that must not enter
+ * an allocator (which may synchronise the device), and plug-ins whose host application
+ * owns the device memory.  Such callers cannot create a plan, so the probe and medium are
+ * passed directly; the caller still passes the input and output arrays (device memory,
+ * as for simus_rf).  Every temporary lives in one fixed device array of
+ * SIMUS_NOALLOC_SCRATCH_BYTES that each device loading the library holds until the
+ * process exits; problems whose temporaries (sub-element table, transfer values,
+ * transmit weights T*bins*N*8 bytes, spectrum T*N*bins*8 bytes and at least one partial
+ * spectrum of the same size) do not fit are rejected with SIMUS_ERR_ARG before any
+ * device work.  The first call on each device resolves the array's address
+ * (cudaGetSymbolAddress) with that device current: make it before any stream capture.
+ * All calls share the array and each keeps the previous call's contents; calls whose
+ * kernels overlap on the GPU race on it (host threads are serialised, streams are not).
+ * No cudaMalloc, cudaFree or allocating library routine is called. */
+#define SIMUS_NOALLOC_SCRATCH_BYTES (32u << 20)
+int simus_rf_noalloc(const simus_probe *probe, const simus_medium *medium, int32_t n_samples,
+                     const simus_tx *tx, const simus_scat *scat, float *rf, void *stream);
+
 /* Message of the calling thread's last error ("" if none). */
 const char *simus_last_error(void);
 

@@ -7,6 +7,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "simus_internal.h"
@@ -170,6 +171,111 @@ int workspace(simus_plan *plan, size_t bytes, void **ptr) {
     return SIMUS_OK;
 }
 
+// Host part of a plan: validation, nu (Eq. 21), kept bins and the Green's constants.
+// Fills every field of *p except the device pointers, the device and the SM count.
+int plan_setup_host(const simus_probe *probe, const simus_medium *medium, int32_t n_samples,
+                    int32_t path, simus_plan *p) {
+    int rc = validate_probe(probe, medium);
+    if (rc) return rc;
+    if (n_samples < 8 || n_samples > (1 << 24))
+        return fail(SIMUS_ERR_ARG, "n_samples=%d outside [8, 2^24]", n_samples);
+    if (path < SIMUS_PATH_PLAIN_F32 || path > SIMUS_PATH_TC_BF16)
+        return fail(SIMUS_ERR_ARG, "unknown path %d", path);
+    p->probe = *probe;
+    p->medium = *medium;
+    p->nt = n_samples;
+    p->path = path;
+    p->N = probe->n_elements;
+    p->nu = resolve_nsub(*probe, *medium);
+    p->M = p->nu * p->N;
+    if (p->M > 8192) return fail(SIMUS_ERR_ARG, "nu * N = %d > 8192", p->M);
+
+    // Kept bins: contiguous range where |S_P S_T| >= 1e-5 max over 1 <= q < Nt/2.
+    const double df = medium->fs / n_samples;
+    const int q_max = (n_samples - 1) / 2;
+    auto mag = [&](int q) {
+        double w = 2.0 * M_PI * q * df, re, im;
+        pulse(*probe, *medium, w, re, im);
+        return std::hypot(re, im) * transducer(*probe, w);
+    };
+    double hmax = 0.0;
+    for (int q = 1; q <= q_max; ++q) hmax = std::max(hmax, mag(q));
+    int lo = -1, hi = -1;
+    for (int q = 1; q <= q_max; ++q)
+        if (mag(q) >= 1e-5 * hmax) { if (lo < 0) lo = q; hi = q; }
+    if (lo < 0) return fail(SIMUS_ERR_ARG, "no frequency bin above threshold (Nt too small?)");
+    p->q_lo = lo;
+    p->q_hi = hi;
+    p->nq = hi - lo + 1;
+    if ((double)hi * n_samples > 16777216.0 * 64)
+        return fail(SIMUS_ERR_ARG, "bin index too large for the exact phase reduction");
+
+    const double b = probe->width / 2.0;
+    const int N = p->N, nu = p->nu;
+    GreenConst &gc = p->gc;
+    gc = GreenConst{};
+    gc.N = N; gc.nu = nu; gc.M = p->M; gc.q_lo = lo; gc.nq = p->nq; gc.nt = n_samples;
+    gc.baffle = probe->baffle;
+    const double K = df / medium->c;                       // cycles per metre per bin
+    gc.Kh = (float)K;
+    gc.Kl = (float)(K - (double)gc.Kh);
+    gc.k1 = (float)(2.0 * M_PI * K);
+    gc.k1b = (float)(2.0 * M_PI * K * b / nu);
+    gc.kh = (float)(M_PI * K);
+    gc.inv_rf = std::isinf(probe->elev_focus) ? 0.f : (float)(1.0 / probe->elev_focus);
+    // Eq. 40: k_a = alpha_dB / 8.69 * f * 1e-4 per metre; base 2 per bin.
+    gc.att2 = (float)(medium->alpha_db / 8.69 * df * 1e-4 / std::log(2.0));
+    gc.zeta = (float)probe->zeta;
+    const double h2 = probe->height * probe->height;
+    for (int g = 0; g < 4; ++g) {
+        gc.ga[g] = (float)(kBre[g] / h2);
+        gc.gb[g] = (float)(kBim[g] / h2);
+        gc.ga2[g] = (float)((kBre[g] / h2) * (kBre[g] / h2));
+        gc.Cr[g] = (float)(kAre[g] * std::sqrt(M_PI / 2.0));
+        gc.Ci[g] = (float)(kAim[g] * std::sqrt(M_PI / 2.0));
+    }
+    gc.narrow = (2.0 * M_PI * K * b / nu) * hi <= 3.19 ? 1 : 0;
+    gc.df = df;
+    return SIMUS_OK;
+}
+
+// The plan's tables: sub-element records (Eq. 24; convex: arc of radius R about (0, -R))
+// into sub[M], transfer values H_q = S_P S_T (Eq. 25-28, Eq. 34) into H[nq].
+void plan_fill_tables(const simus_plan *p, SubElem *sub, float2 *H) {
+    const simus_probe &probe = p->probe;
+    for (int k = 0; k < p->nq; ++k) {
+        double w = 2.0 * M_PI * (p->q_lo + k) * p->gc.df, re, im;
+        pulse(probe, p->medium, w, re, im);
+        double st = transducer(probe, w);
+        H[k] = make_float2((float)(re * st), (float)(im * st));
+    }
+    const double b = probe.width / 2.0;
+    const int N = p->N, nu = p->nu;
+    for (int e = 0; e < N; ++e)
+        for (int mu = 0; mu < nu; ++mu) {
+            double xc, zc, psi;
+            const double off = b / nu * (2.0 * mu - nu + 1);
+            if (probe.radius > 0) {
+                const double R = probe.radius;
+                psi = (e - (N - 1) / 2.0) * probe.pitch / R + off / R;
+                xc = R * std::sin(psi);
+                zc = R * std::cos(psi) - R;
+            } else {
+                psi = 0.0;
+                xc = probe.pitch / 2.0 * (2.0 * (e + 1) - N - 1) + off;
+                zc = 0.0;
+            }
+            SubElem &s = sub[e * nu + mu];
+            s.xh = (float)xc;
+            s.xl = (float)(xc - (double)s.xh);
+            s.zh = (float)zc;
+            s.zl = (float)(zc - (double)s.zh);
+            s.cpsi = (float)std::cos(psi);
+            s.spsi = (float)std::sin(psi);
+            s.pad0 = s.pad1 = 0.f;
+        }
+}
+
 }  // namespace simus
 
 extern "C" {
@@ -205,105 +311,12 @@ int simus_plan_create(const simus_probe *probe, const simus_medium *medium, int3
                       int32_t path, simus_plan **out) {
     if (!out) return fail(SIMUS_ERR_ARG, "out must not be NULL");
     *out = nullptr;
-    int rc = validate_probe(probe, medium);
-    if (rc) return rc;
-    if (n_samples < 8 || n_samples > (1 << 24))
-        return fail(SIMUS_ERR_ARG, "n_samples=%d outside [8, 2^24]", n_samples);
-    if (path < SIMUS_PATH_PLAIN_F32 || path > SIMUS_PATH_TC_BF16)
-        return fail(SIMUS_ERR_ARG, "unknown path %d", path);
-
     simus_plan *p = new simus_plan();
-    p->probe = *probe;
-    p->medium = *medium;
-    p->nt = n_samples;
-    p->path = path;
-    p->N = probe->n_elements;
-    p->nu = resolve_nsub(*probe, *medium);
-    p->M = p->nu * p->N;
-    if (p->M > 8192) { delete p; return fail(SIMUS_ERR_ARG, "nu * N = %d > 8192", p->M); }
-
-    // Kept bins: contiguous range where |S_P S_T| >= 1e-5 max over 1 <= q < Nt/2.
-    const double df = medium->fs / n_samples;
-    const int q_max = (n_samples - 1) / 2;
-    std::vector<double> mag(q_max + 1, 0.0);
-    double hmax = 0.0;
-    for (int q = 1; q <= q_max; ++q) {
-        double w = 2.0 * M_PI * q * df, re, im;
-        pulse(*probe, *medium, w, re, im);
-        mag[q] = std::hypot(re, im) * transducer(*probe, w);
-        hmax = std::max(hmax, mag[q]);
-    }
-    int lo = -1, hi = -1;
-    for (int q = 1; q <= q_max; ++q)
-        if (mag[q] >= 1e-5 * hmax) { if (lo < 0) lo = q; hi = q; }
-    if (lo < 0) { delete p; return fail(SIMUS_ERR_ARG, "no frequency bin above threshold (Nt too small?)"); }
-    p->q_lo = lo;
-    p->q_hi = hi;
-    p->nq = hi - lo + 1;
-    if ((double)hi * n_samples > 16777216.0 * 64) {
-        delete p;
-        return fail(SIMUS_ERR_ARG, "bin index too large for the exact phase reduction");
-    }
-
-    std::vector<float2> H(p->nq);
-    for (int k = 0; k < p->nq; ++k) {
-        double w = 2.0 * M_PI * (lo + k) * df, re, im;
-        pulse(*probe, *medium, w, re, im);
-        double st = transducer(*probe, w);
-        H[k] = make_float2((float)(re * st), (float)(im * st));
-    }
-
-    // Sub-element centroids (Eq. 24; convex: arc of radius R about (0, -R)).
+    int rc = plan_setup_host(probe, medium, n_samples, path, p);
+    if (rc) { delete p; return rc; }
     std::vector<SubElem> sub(p->M);
-    const double b = probe->width / 2.0;
-    const int N = p->N, nu = p->nu;
-    for (int e = 0; e < N; ++e)
-        for (int mu = 0; mu < nu; ++mu) {
-            double xc, zc, psi;
-            const double off = b / nu * (2.0 * mu - nu + 1);
-            if (probe->radius > 0) {
-                const double R = probe->radius;
-                psi = (e - (N - 1) / 2.0) * probe->pitch / R + off / R;
-                xc = R * std::sin(psi);
-                zc = R * std::cos(psi) - R;
-            } else {
-                psi = 0.0;
-                xc = probe->pitch / 2.0 * (2.0 * (e + 1) - N - 1) + off;
-                zc = 0.0;
-            }
-            SubElem &s = sub[e * nu + mu];
-            s.xh = (float)xc;
-            s.xl = (float)(xc - (double)s.xh);
-            s.zh = (float)zc;
-            s.zl = (float)(zc - (double)s.zh);
-            s.cpsi = (float)std::cos(psi);
-            s.spsi = (float)std::sin(psi);
-            s.pad0 = s.pad1 = 0.f;
-        }
-
-    GreenConst &gc = p->gc;
-    gc.N = N; gc.nu = nu; gc.M = p->M; gc.q_lo = lo; gc.nq = p->nq; gc.nt = n_samples;
-    gc.baffle = probe->baffle;
-    const double K = df / medium->c;                       // cycles per metre per bin
-    gc.Kh = (float)K;
-    gc.Kl = (float)(K - (double)gc.Kh);
-    gc.k1 = (float)(2.0 * M_PI * K);
-    gc.k1b = (float)(2.0 * M_PI * K * b / nu);
-    gc.kh = (float)(M_PI * K);
-    gc.inv_rf = std::isinf(probe->elev_focus) ? 0.f : (float)(1.0 / probe->elev_focus);
-    // Eq. 40: k_a = alpha_dB / 8.69 * f * 1e-4 per metre; base 2 per bin.
-    gc.att2 = (float)(medium->alpha_db / 8.69 * df * 1e-4 / std::log(2.0));
-    gc.zeta = (float)probe->zeta;
-    const double h2 = probe->height * probe->height;
-    for (int g = 0; g < 4; ++g) {
-        gc.ga[g] = (float)(kBre[g] / h2);
-        gc.gb[g] = (float)(kBim[g] / h2);
-        gc.ga2[g] = (float)((kBre[g] / h2) * (kBre[g] / h2));
-        gc.Cr[g] = (float)(kAre[g] * std::sqrt(M_PI / 2.0));
-        gc.Ci[g] = (float)(kAim[g] * std::sqrt(M_PI / 2.0));
-    }
-    gc.narrow = (2.0 * M_PI * K * b / nu) * hi <= 3.19 ? 1 : 0;
-    gc.df = df;
+    std::vector<float2> H(p->nq);
+    plan_fill_tables(p, sub.data(), H.data());
 
     cudaError_t e = cudaGetDevice(&p->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
@@ -533,3 +546,116 @@ int simus_batch_rf(int32_t n_sims, simus_plan *const *plans, const simus_tx *tx,
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------
+// simus_rf_noalloc: the plain FP32 RF computation with no device allocation.
+//
+// Some callers cannot allocate device memory: code that runs while a stream is being
+// captured in global capture mode (where cudaMalloc is refused), latency-critical loops
+// that must never enter the allocator (which can synchronise the device), and plug-ins
+// hosted by an application that owns the whole device memory pool.  They cannot create
+// a plan either, so this entry point takes the probe and medium directly and keeps every
+// temporary -- sub-element table, transfer values, transmit weights, per-chunk partial
+// spectra and the spectrum -- in one file-scope device array of fixed size.
+//
+// The array exists once per device that loads the library and lives until the process
+// exits.  Host code cannot use the array's name as a device address, so the first call
+// on each device (with that device current) resolves the address with
+// cudaGetSymbolAddress and caches it; make that first call before any stream capture.
+// Every call shares the array: calls that overlap on the GPU (other streams, or other
+// host threads whose kernels are still running) race on it.  Calls from several host
+// threads are serialised on the host.  Nothing in the array must start at zero: every
+// buffer is fully written before it is read.
+// ---------------------------------------------------------------------------------
+namespace {
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[SIMUS_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kNoallocMaxDevices = 64;
+constexpr int kNoallocMaxSub = 2048;     // nu * N
+constexpr int kNoallocMaxBins = 16384;   // kept bins
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[kNoallocMaxDevices] = {};
+int g_noalloc_sms[kNoallocMaxDevices] = {};
+SubElem g_noalloc_sub[kNoallocMaxSub];   // host staging of the tables (no allocation)
+float2 g_noalloc_H[kNoallocMaxBins];
+
+}  // namespace
+
+extern "C" int simus_rf_noalloc(const simus_probe *probe, const simus_medium *medium,
+                                int32_t n_samples, const simus_tx *tx, const simus_scat *scat,
+                                float *rf, void *stream) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    int dev = 0, rc;
+    if ((rc = check_cuda(cudaGetDevice(&dev), "cudaGetDevice"))) return rc;
+    if (dev < 0 || dev >= kNoallocMaxDevices)
+        return fail(SIMUS_ERR_ARG, "device %d beyond the %d this entry point serves", dev, kNoallocMaxDevices);
+    if (!g_noalloc_addr[dev]) {   // once per device, with that device current
+        void *addr = nullptr;
+        if ((rc = check_cuda(cudaGetSymbolAddress(&addr, g_noalloc_scratch), "cudaGetSymbolAddress")))
+            return rc;
+        if ((rc = check_cuda(cudaDeviceGetAttribute(&g_noalloc_sms[dev], cudaDevAttrMultiProcessorCount, dev),
+                             "SM count")))
+            return rc;
+        g_noalloc_addr[dev] = addr;
+    }
+
+    simus_plan plan;   // host-only description; its table pointers point into the scratch
+    if ((rc = plan_setup_host(probe, medium, n_samples, SIMUS_PATH_PLAIN_F32, &plan))) return rc;
+    plan.device = dev;
+    plan.num_sms = g_noalloc_sms[dev];
+    if (plan.M > kNoallocMaxSub || plan.nq > kNoallocMaxBins)
+        return fail(SIMUS_ERR_ARG, "simus_rf_noalloc serves nu*N <= %d and <= %d kept bins (got %d, %d)",
+                    kNoallocMaxSub, kNoallocMaxBins, plan.M, plan.nq);
+    if ((rc = validate_tx(&plan, tx))) return rc;
+    if ((rc = validate_scat(scat))) return rc;
+    if ((rc = check_device_ptr(rf, "rf"))) return rc;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int T = tx->n_tx, n_chan = T * plan.N;
+    if (scat->n == 0)
+        return check_cuda(cudaMemsetAsync(rf, 0, sizeof(float) * (size_t)n_chan * plan.nt, st), "memset rf");
+
+    // scratch layout: [sub | H | weights | spectrum | partials (as many chunks as fit)]
+    const size_t sub_b = align256(sizeof(SubElem) * plan.M);
+    const size_t h_b = align256(sizeof(float2) * plan.nq);
+    const size_t cw_b = align256(sizeof(float2) * (size_t)T * plan.nq * plan.N);
+    const size_t spec_b = align256(sizeof(float2) * (size_t)n_chan * plan.nq);
+    const size_t per_chunk = sizeof(float2) * (size_t)n_chan * plan.nq;
+    const size_t fixed = sub_b + h_b + cw_b + spec_b;
+    if (fixed + per_chunk > SIMUS_NOALLOC_SCRATCH_BYTES)
+        return fail(SIMUS_ERR_ARG,
+                    "problem needs at least %zu bytes of scratch, more than the fixed %u of "
+                    "simus_rf_noalloc (use simus_rf with a plan)",
+                    fixed + per_chunk, (unsigned)SIMUS_NOALLOC_SCRATCH_BYTES);
+    const int64_t max_chunks = (int64_t)((SIMUS_NOALLOC_SCRATCH_BYTES - fixed) / per_chunk);
+
+    PlainGeom g = plain_geometry(&plan, T, scat->n);
+    if (g.n_chunks > max_chunks) {
+        int64_t len = (scat->n + max_chunks - 1) / max_chunks;
+        len = ((len + g.SB - 1) / g.SB) * g.SB;
+        g.chunk_len = len;
+        g.n_chunks = (int)((scat->n + len - 1) / len);
+    }
+
+    char *base = reinterpret_cast<char *>(g_noalloc_addr[dev]);
+    SubElem *d_sub = reinterpret_cast<SubElem *>(base);
+    float2 *d_H = reinterpret_cast<float2 *>(base + sub_b);
+    float2 *cw = reinterpret_cast<float2 *>(base + sub_b + h_b);
+    float2 *spec = reinterpret_cast<float2 *>(base + sub_b + h_b + cw_b);
+    float2 *part = reinterpret_cast<float2 *>(base + fixed);
+
+    plan_fill_tables(&plan, g_noalloc_sub, g_noalloc_H);
+    // pageable source: the copies have read the host staging when these calls return
+    if ((rc = check_cuda(cudaMemcpyAsync(d_sub, g_noalloc_sub, sizeof(SubElem) * plan.M,
+                                         cudaMemcpyHostToDevice, st), "upload sub-elements")))
+        return rc;
+    if ((rc = check_cuda(cudaMemcpyAsync(d_H, g_noalloc_H, sizeof(float2) * plan.nq,
+                                         cudaMemcpyHostToDevice, st), "upload transfer values")))
+        return rc;
+    plan.d_sub = d_sub;
+    plan.d_H = d_H;
+    if ((rc = launch_tx_weights(&plan, tx, cw, st))) return rc;
+    if ((rc = launch_plain(&plan, g, scat, T, cw, part, st))) return rc;
+    if ((rc = launch_reduce_spectrum(&plan, part, g.n_chunks, n_chan, spec, st))) return rc;
+    return launch_idft(&plan, spec, n_chan, rf, st);
+}

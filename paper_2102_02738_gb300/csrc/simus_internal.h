@@ -69,6 +69,12 @@ namespace simus {
 // plan's workspace (synchronising the device before a reallocation).
 int workspace(simus_plan *plan, size_t bytes, void **ptr);
 
+// Host part of a plan (validation, nu, kept bins, Green's constants; no device work)
+// and its two tables (sub-element records [M], transfer values [nq]).
+int plan_setup_host(const simus_probe *probe, const simus_medium *medium, int32_t n_samples,
+                    int32_t path, simus_plan *p);
+void plan_fill_tables(const simus_plan *p, SubElem *sub, float2 *H);
+
 // Tracing: events around a stage (no-ops unless profiling is enabled) and the
 // process-wide launch counter.
 void stage_begin(simus_plan *plan, int stage, cudaStream_t st);

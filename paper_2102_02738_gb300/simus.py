@@ -86,6 +86,9 @@ def _load():
     L.simus_plan_get_timings.argtypes = [vp, C.POINTER(C.c_float)]
     L.simus_kernel_launches.restype = i64
     L.simus_kernel_launches.argtypes = []
+    L.simus_plan_check.argtypes = [vp]
+    L.simus_rf_noalloc.argtypes = [C.POINTER(Probe), C.POINTER(Medium), i32, C.POINTER(Tx),
+                                   C.POINTER(Scat), vp, vp]
     return L
 
 
@@ -201,6 +204,18 @@ def simus_rf_grad(h, delays, apod, x, y, z, rc, drf, g_rc=None, g_x=None, g_z=No
                              C.byref(scat_struct(x, y, z, rc)), _dev(drf, "drf"),
                              _dev(g_rc, "g_rc"), _dev(g_x, "g_x"), _dev(g_z, "g_z"),
                              _dev(g_delays, "g_delays"), _stream(stream)))
+
+
+def simus_plan_check(h):
+    _check(lib.simus_plan_check(h))
+
+
+def simus_rf_noalloc(cfg, n_samples, delays, apod, x, y, z, rc, rf, stream=None):
+    """simus_rf without device allocation (fixed per-device scratch; see simus.h)."""
+    _check(lib.simus_rf_noalloc(C.byref(probe_struct(cfg)), C.byref(medium_struct(cfg)),
+                                int(n_samples), C.byref(tx_struct(delays, apod)),
+                                C.byref(scat_struct(x, y, z, rc)), _dev(rf, "rf"),
+                                _stream(stream)))
 
 
 def simus_plan_set_profiling(h, enable=True):
