@@ -37,9 +37,9 @@ WORKLOADS = {
     "focused-linear-64": ph.focused_linear_64,
     "planewave-linear-128-grad": ph.planewave_linear_128_grad,
 }
-DEFAULT_WORKLOAD = "planewave-linear-128"
+DEFAULT_WORKLOAD = "diverging-convex-128"
 DEFAULT_PATH = {"planewave-linear-128": "plain", "focused-linear-64": "plain",
-                "planewave-linear-128-grad": "plain", "diverging-convex-128": "plain"}
+                "planewave-linear-128-grad": "plain", "diverging-convex-128": "tc_f16"}
 # Per-term instruction budget of the Green's term (FP32 pipe, MUFU) used for the ALU
 # roofline: 85 FP32-pipe instructions + 12 MUFU per (bin, scatterer, sub-element).
 FP32_PER_TERM, MUFU_PER_TERM = 85, 12
@@ -145,7 +145,7 @@ def allreduce_max(v, ws):
 # --------------------------------------------------------------------- CPU oracle
 def oracle_sample(w, target_s=12.0, max_bins=None):
     """Time the oracle's RF spectrum on a subset of kept bins (all scatterers, all
-    transmits); returns (terms/s, seconds, bins used, threads)."""
+    transmits); returns (terms/s, seconds, bins used, threads, bin list, spectrum)."""
     from oracle import oracle
     lo, hi, nb = oracle.bins(w.cfg)
     nu = oracle.nsub(w.cfg)
@@ -155,7 +155,7 @@ def oracle_sample(w, target_s=12.0, max_bins=None):
     k = max(1, min(nb, cores))
     qs = np.linspace(lo, hi, k).round().astype(int)
     t0 = time.perf_counter()
-    oracle.rf_spectrum(w.cfg, w.delays, w.apod, w.x, w.y, w.z, w.rc, qs)
+    X = oracle.rf_spectrum(w.cfg, w.delays, w.apod, w.x, w.y, w.z, w.rc, qs)
     dt = time.perf_counter() - t0
     if dt < target_s:
         k2 = int(min(nb, max(k, k * target_s / max(dt, 1e-3))))
@@ -165,10 +165,10 @@ def oracle_sample(w, target_s=12.0, max_bins=None):
         if k2 > k:
             qs = np.linspace(lo, hi, k2).round().astype(int)
             t0 = time.perf_counter()
-            oracle.rf_spectrum(w.cfg, w.delays, w.apod, w.x, w.y, w.z, w.rc, qs)
+            X = oracle.rf_spectrum(w.cfg, w.delays, w.apod, w.x, w.y, w.z, w.rc, qs)
             dt = time.perf_counter() - t0
             k = k2
-    return k * per_bin / dt, dt, k, cores
+    return k * per_bin / dt, dt, k, cores, qs, X
 
 
 def run_reference(args, rank, ws):
@@ -181,7 +181,7 @@ def run_reference(args, rank, ws):
     per_bin = w.n_scat * nu * w.cfg["n_elements"] * w.n_tx
     cores = len(os.sched_getaffinity(0))
     # each step: a fixed bin subset sized for ~3 s, so K + W steps stay within minutes
-    _, dt1, k1, _ = oracle_sample(w, target_s=0.0)
+    _, dt1, k1, _, _, _ = oracle_sample(w, target_s=0.0)
     per_step_bins = max(1, min(nb, int(k1 * 3.0 / max(dt1, 1e-3))))
     qs = np.linspace(lo, hi, per_step_bins).round().astype(int)
     for _ in range(args.warmup):
@@ -296,12 +296,37 @@ def run_ours(args, rank, ws, local):
     e2e_ms = allreduce_max(e2e_ms, ws) / e2e_steps
     e2e_value = terms * ws / (e2e_ms / 1e3)
 
+    # the plain FP32 path on the same workload (one step) for the tensor-core speed-up
+    plain = None
+    if path != "plain" and not args.no_plain_compare:
+        pplan = simus.Plan(w.cfg, path="plain")
+        simus.simus_plan_set_profiling(pplan.handle, True)
+        pplan.rf(d["delays"], d["apod"], d["x"], None, d["z"], d["rc"], out=rf, stream=stream)
+        torch.cuda.synchronize()
+        flush.fill_(0.5)
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        pplan.rf(d["delays"], d["apod"], d["x"], None, d["z"], d["rc"], out=rf, stream=stream)
+        p1.record(stream)
+        p1.synchronize()
+        pms = p0.elapsed_time(p1)
+        plain = {"value": terms / (pms / 1e3), "unit": "terms/s", "ms_per_step": pms,
+                 "kernel_ms": simus.simus_plan_get_timings(pplan.handle)["green_contract"],
+                 "speedup_of_this_path": (pms / ms_per_step)}
+        pplan.close()
+
     cpu = None
+    accuracy = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        v, dt, k, cores = oracle_sample(w, target_s=args.cpu_seconds)
+        v, dt, k, cores, qs, Xo = oracle_sample(w, target_s=args.cpu_seconds)
         cpu = {"value": v, "unit": "terms/s", "cores": cores, "kind": "oracle",
                "sample": f"RF spectrum at {k} of {info['n_bins']} kept bins, all "
                          f"{w.n_scat} scatterers and {T} transmits, FP64, {dt:.1f} s"}
+        spec = plan.rf_spectrum(d["delays"], d["apod"], d["x"], None, d["z"], d["rc"])
+        Xg = spec.cpu().numpy()[..., qs - info["q_lo"]]
+        accuracy = {"rel_l2_vs_fp64_oracle": float(np.linalg.norm(Xg - Xo) / np.linalg.norm(Xo)),
+                    "compared": f"RF spectra X_q(e,t) at the {k} sampled bins, every element "
+                                f"and transmit", "tolerance": 1e-5 if path == "plain" else 2e-3}
 
     line = {
         "metric": METRIC, "value": value, "unit": "terms/s", "n_gpus": ws,
@@ -329,6 +354,10 @@ def run_ours(args, rank, ws, local):
     }
     if cpu is not None:
         line["cpu_baseline"] = cpu
+    if accuracy is not None:
+        line["accuracy"] = accuracy
+    if plain is not None:
+        line["plain_f32_same_workload"] = plain
     if rank == 0:
         print(json.dumps(line), flush=True)
     plan.close()
@@ -344,6 +373,7 @@ def main():
     ap.add_argument("--path", default=None, choices=[None, "plain", "tc_f16", "tc_bf16"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain-compare", action="store_true")
     ap.add_argument("--n-scat", type=int, default=0,
                     help="override the workload's scatterer count (profiling of small cases)")
     args = ap.parse_args()

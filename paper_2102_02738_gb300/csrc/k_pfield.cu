@@ -1,0 +1,124 @@
+// k_pfield.cu -- RMS pressure field (Eq. 22, Eq. 41-42) on the CUDA cores, FP32.
+//
+//   P(X, w_j) = P_Tx(w_j) sum_n W_n g_n(X, w_j) exp(i w_j dtau_n),
+//   P_RMS(X)  = sqrt(dw sum_j |P(X, w_j)|^2),   w_j = (j + 1/2) dw,  dw = 2 w_c / N_f.
+// Since only |P|^2 enters, the pulse contributes |P_Tx|^2 = |S_P|^2 S_T per frequency.
+// The midpoint frequencies are f_j = (j + 1/2) df with df = 2 fc / N_f, so the Green's
+// machinery runs with half-integer "bin indices" q = j + 1/2 and that df.
+//
+// Thread per field point; frequencies in runs of QB (phase recurrence over the run),
+// all sub-elements accumulated per run, then |.|^2 weighted and summed.  Frequencies
+// whose |P_Tx|^2 is below 1e-12 of its maximum are skipped (their share of the sum is
+// below 1e-12 N_f relative).
+#include <algorithm>
+
+#include "green.cuh"
+#include "simus_internal.h"
+
+namespace simus {
+
+namespace {
+constexpr int kPThreads = 256;
+constexpr int kPQB = 8;
+}  // namespace
+
+// wt[t][jj][e] = W_te exp(i 2 pi frac((j0 + jj + 1/2) df dtau_te)), FP64 phase reduction.
+__global__ void k_pfield_weights(int T, int N, int nf, int j0, double df,
+                                 const float *__restrict__ delays, const float *__restrict__ apod,
+                                 float2 *__restrict__ wt) {
+    const int64_t total = (int64_t)T * nf * N;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int e = (int)(i % N);
+        const int64_t r = i / N;
+        const int jj = (int)(r % nf), t = (int)(r / nf);
+        double ph = ((double)(j0 + jj) + 0.5) * ((double)delays[t * N + e] * df);
+        ph -= rint(ph);
+        float s, c;
+        sincospif((float)(2.0 * ph), &s, &c);
+        const float w = apod[t * N + e];
+        wt[i] = make_float2(w * c, w * s);
+    }
+}
+
+template <bool HAS_Y, bool NARROW>
+__global__ void __launch_bounds__(kPThreads, 2)
+k_pfield(const GreenConst gc, const SubElem *__restrict__ sub_g, const float *__restrict__ xg,
+         const float *__restrict__ yg, const float *__restrict__ zg, int64_t npts, int nf, int j0,
+         const float2 *__restrict__ wt, const float *__restrict__ ptx2, float dw,
+         float *__restrict__ prms) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int N = gc.N, nu = gc.nu, M = gc.M;
+    const int tid = threadIdx.x, t = blockIdx.y;
+    SubElem *sub = reinterpret_cast<SubElem *>(smem_raw);      // [M]
+    float2 *wtt = reinterpret_cast<float2 *>(sub + M);         // [QB][N]
+    for (int i = tid; i < M; i += kPThreads) sub[i] = sub_g[i];
+
+    const int64_t i = blockIdx.x * (int64_t)kPThreads + tid;
+    const bool live = i < npts;
+    const float xs = live ? xg[i] : 0.f, zs = live ? zg[i] : 1.f;
+    const float ys = (HAS_Y && live) ? yg[i] : 0.f;
+    float power = 0.f;
+    for (int jb = 0; jb < nf; jb += kPQB) {
+        __syncthreads();
+        for (int k = tid; k < kPQB * N; k += kPThreads) {
+            const int jj = k / N, e = k - jj * N;
+            wtt[k] = jb + jj < nf ? wt[((size_t)t * nf + jb + jj) * N + e] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        const float q0 = (float)(j0 + jb) + 0.5f;
+        float ar[kPQB], ai[kPQB];
+#pragma unroll
+        for (int j = 0; j < kPQB; ++j) ar[j] = ai[j] = 0.f;
+        for (int n = 0; n < M; ++n) {
+            const int e = n / nu;
+            PairSetup P = pair_setup<HAS_Y>(gc, sub[n], xs, ys, zs, q0);
+            PhaseRun R = phase_run(P, q0);
+#pragma unroll
+            for (int j = 0; j < kPQB; ++j) {
+                const float q = q0 + (float)j;
+                const float m = sinc_f<NARROW>(q * P.xb);
+                const float2 d = delta_f<HAS_Y>(gc, P, q);
+                const float er = R.zr * m, ei = R.zi * m;
+                const float gr = er * d.x - ei * d.y, gi = er * d.y + ei * d.x;
+                const float2 w = wtt[j * N + e];
+                ar[j] = fmaf(w.x, gr, fmaf(-w.y, gi, ar[j]));
+                ai[j] = fmaf(w.x, gi, fmaf(w.y, gr, ai[j]));
+                const float nzr = fmaf(R.zr, R.wr, -R.zi * R.wi);
+                R.zi = fmaf(R.zr, R.wi, R.zi * R.wr);
+                R.zr = nzr;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kPQB; ++j)
+            if (jb + j < nf) power = fmaf(ptx2[jb + j], ar[j] * ar[j] + ai[j] * ai[j], power);
+    }
+    if (live) prms[(size_t)t * npts + i] = sqrtf(dw * power);
+}
+
+int launch_pfield(const simus_plan *p, const GreenConst &gc, const simus_tx *tx, int64_t npts,
+                  const float *x, const float *y, const float *z, int nf, int j0, float2 *wt,
+                  const float *ptx2, float dw, float *prms, cudaStream_t st) {
+    const int T = tx->n_tx;
+    {
+        int64_t total = (int64_t)T * nf * p->N;
+        int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)p->num_sms * 8);
+        k_pfield_weights<<<std::max(blocks, 1), 256, 0, st>>>(T, p->N, nf, j0, gc.df, tx->delays,
+                                                               tx->apod, wt);
+        count_launches(1);
+        int rc = check_cuda(cudaGetLastError(), "k_pfield_weights launch");
+        if (rc) return rc;
+    }
+    const size_t smem = sizeof(SubElem) * p->M + sizeof(float2) * (size_t)kPQB * p->N;
+    const bool has_y = y != nullptr, narrow = gc.narrow != 0;
+    auto kern = has_y ? (narrow ? k_pfield<true, true> : k_pfield<true, false>)
+                      : (narrow ? k_pfield<false, true> : k_pfield<false, false>);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return check_cuda(e, "k_pfield smem attribute");
+    dim3 grid((unsigned)((npts + kPThreads - 1) / kPThreads), T);
+    kern<<<grid, kPThreads, smem, st>>>(gc, p->d_sub, x, y, z, npts, nf, j0, wt, ptx2, dw, prms);
+    count_launches(1);
+    return check_cuda(cudaGetLastError(), "k_pfield launch");
+}
+
+}  // namespace simus

@@ -210,11 +210,22 @@ int plan_setup_host(const simus_probe *probe, const simus_medium *medium, int32_
     if ((double)hi * n_samples > 16777216.0 * 64)
         return fail(SIMUS_ERR_ARG, "bin index too large for the exact phase reduction");
 
+    p->gc = green_const(*probe, *medium, p->N, p->nu, df, hi);
+    p->gc.q_lo = lo;
+    p->gc.nq = p->nq;
+    p->gc.nt = n_samples;
+    return SIMUS_OK;
+}
+
+// Green's constants for bin spacing df (frequency of "bin" q is q df; q may be
+// fractional), with the narrow-sinc flag valid for bins up to q_max.
+GreenConst green_const(const simus_probe &pr, const simus_medium &md, int N, int nu, double df,
+                       double q_max) {
+    const simus_probe *probe = &pr;
+    const simus_medium *medium = &md;
     const double b = probe->width / 2.0;
-    const int N = p->N, nu = p->nu;
-    GreenConst &gc = p->gc;
-    gc = GreenConst{};
-    gc.N = N; gc.nu = nu; gc.M = p->M; gc.q_lo = lo; gc.nq = p->nq; gc.nt = n_samples;
+    GreenConst gc{};
+    gc.N = N; gc.nu = nu; gc.M = N * nu;
     gc.baffle = probe->baffle;
     const double K = df / medium->c;                       // cycles per metre per bin
     gc.Kh = (float)K;
@@ -234,9 +245,9 @@ int plan_setup_host(const simus_probe *probe, const simus_medium *medium, int32_
         gc.Cr[g] = (float)(kAre[g] * std::sqrt(M_PI / 2.0));
         gc.Ci[g] = (float)(kAim[g] * std::sqrt(M_PI / 2.0));
     }
-    gc.narrow = (2.0 * M_PI * K * b / nu) * hi <= 3.19 ? 1 : 0;
+    gc.narrow = (2.0 * M_PI * K * b / nu) * q_max <= 3.19 ? 1 : 0;
     gc.df = df;
-    return SIMUS_OK;
+    return gc;
 }
 
 // The plan's tables: sub-element records (Eq. 24; convex: arc of radius R about (0, -R))
@@ -524,14 +535,99 @@ int simus_rf(simus_plan *plan, const simus_tx *tx, const simus_scat *scat, float
 
 int simus_pfield(simus_plan *plan, const simus_tx *tx, int64_t n_pts, const float *x,
                  const float *y, const float *z, int32_t n_freq, float *prms, void *stream) {
-    (void)plan; (void)tx; (void)n_pts; (void)x; (void)y; (void)z; (void)n_freq; (void)prms; (void)stream;
-    return fail(SIMUS_ERR_UNSUPPORTED, "simus_pfield not built yet");
+    if (!plan) return fail(SIMUS_ERR_ARG, "plan must not be NULL");
+    for (bool &u : plan->stage_used) u = false;
+    int rc;
+    if ((rc = use_plan_device(plan))) return rc;
+    if ((rc = validate_tx(plan, tx))) return rc;
+    if (n_pts < 0 || n_pts > ((int64_t)1 << 31)) return fail(SIMUS_ERR_ARG, "n_pts out of range");
+    if (n_freq < 1 || n_freq > 1000000) return fail(SIMUS_ERR_ARG, "n_freq=%d outside [1, 1e6]", n_freq);
+    if (n_pts == 0) return SIMUS_OK;
+    if ((rc = check_device_ptr(x, "x")) || (rc = check_device_ptr(y, "y", true)) ||
+        (rc = check_device_ptr(z, "z")) || (rc = check_device_ptr(prms, "prms")))
+        return rc;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const double df = 2.0 * plan->probe.fc / n_freq;            // midpoint grid of Eq. 42 (R8)
+    const double dw = 2.0 * M_PI * df;
+    // |P_Tx|^2 = |S_P|^2 S_T (Eq. 28); keep the contiguous range above 1e-12 of the maximum
+    std::vector<float> p2(n_freq);
+    double pmax = 0.0;
+    for (int j = 0; j < n_freq; ++j) {
+        double w = 2.0 * M_PI * (j + 0.5) * df, re, im;
+        pulse(plan->probe, plan->medium, w, re, im);
+        double v = (re * re + im * im) * transducer(plan->probe, w);
+        p2[j] = (float)v;
+        pmax = std::max(pmax, v);
+    }
+    int j_lo = -1, j_hi = -1;
+    for (int j = 0; j < n_freq; ++j)
+        if (p2[j] >= 1e-12 * pmax) { if (j_lo < 0) j_lo = j; j_hi = j; }
+    if (j_lo < 0) return fail(SIMUS_ERR_ARG, "empty transmit spectrum");
+    const int nf = j_hi - j_lo + 1;
+    GreenConst gc = green_const(plan->probe, plan->medium, plan->N, plan->nu, df, j_hi + 0.5);
+    const int T = tx->n_tx;
+    const size_t wt_b = align256(sizeof(float2) * (size_t)T * nf * plan->N);
+    const size_t p2_b = align256(sizeof(float) * nf);
+    void *ws;
+    if ((rc = workspace(plan, wt_b + p2_b, &ws))) return rc;
+    float2 *wt = reinterpret_cast<float2 *>(ws);
+    float *d_p2 = reinterpret_cast<float *>(reinterpret_cast<char *>(ws) + wt_b);
+    if ((rc = check_cuda(cudaMemcpyAsync(d_p2, p2.data() + j_lo, sizeof(float) * nf,
+                                         cudaMemcpyHostToDevice, st), "upload |P_Tx|^2")))
+        return rc;
+    stage_begin(plan, 4, st);
+    rc = launch_pfield(plan, gc, tx, n_pts, x, y, z, nf, j_lo, wt, d_p2, (float)dw, prms, st);
+    stage_end(plan, 4, st);
+    return rc;
 }
 
 int simus_rf_grad(simus_plan *plan, const simus_tx *tx, const simus_scat *scat, const float *drf,
                   float *g_rc, float *g_x, float *g_z, float *g_delays, void *stream) {
-    (void)plan; (void)tx; (void)scat; (void)drf; (void)g_rc; (void)g_x; (void)g_z; (void)g_delays; (void)stream;
-    return fail(SIMUS_ERR_UNSUPPORTED, "simus_rf_grad not built yet");
+    if (!plan) return fail(SIMUS_ERR_ARG, "plan must not be NULL");
+    for (bool &u : plan->stage_used) u = false;
+    int rc;
+    if ((rc = use_plan_device(plan))) return rc;
+    if ((rc = validate_tx(plan, tx))) return rc;
+    if ((rc = validate_scat(scat))) return rc;
+    if (scat->y) return fail(SIMUS_ERR_ARG, "simus_rf_grad needs scatterers in the azimuth plane (y == NULL)");
+    if ((rc = check_device_ptr(drf, "drf"))) return rc;
+    if ((rc = check_device_ptr(g_rc, "g_rc", true)) || (rc = check_device_ptr(g_x, "g_x", true)) ||
+        (rc = check_device_ptr(g_z, "g_z", true)) || (rc = check_device_ptr(g_delays, "g_delays", true)))
+        return rc;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int T = tx->n_tx;
+    const int64_t S = scat->n;
+    if (S == 0) {
+        if (g_delays)
+            return check_cuda(cudaMemsetAsync(g_delays, 0, sizeof(float) * (size_t)T * plan->N, st),
+                              "memset g_delays");
+        return SIMUS_OK;
+    }
+    GradGeom g = grad_geometry(plan, T, S);
+    if (!g.ok) return fail(SIMUS_ERR_UNSUPPORTED, "simus_rf_grad needs T * N <= 2048 (T=%d, N=%d)", T, plan->N);
+    const size_t tab = align256(sizeof(float2) * (size_t)T * plan->nq * plan->N);
+    const size_t gp = align256(sizeof(float) * 3 * (size_t)g.n_qtiles * S);
+    const size_t bp = align256(sizeof(float2) * (size_t)g.n_chunks * T * plan->nq * plan->N);
+    void *ws;
+    if ((rc = workspace(plan, 2 * tab + gp + bp, &ws))) return rc;
+    char *base = reinterpret_cast<char *>(ws);
+    float2 *cw = reinterpret_cast<float2 *>(base);
+    float2 *lam = reinterpret_cast<float2 *>(base + tab);
+    float *gpart = reinterpret_cast<float *>(base + 2 * tab);
+    float2 *bpart = reinterpret_cast<float2 *>(base + 2 * tab + gp);
+    stage_begin(plan, 0, st);
+    if ((rc = launch_tx_weights(plan, tx, cw, st))) return rc;
+    stage_end(plan, 0, st);
+    stage_begin(plan, 5, st);
+    if ((rc = launch_adjoint_dft(plan, drf, T, lam, st))) return rc;
+    stage_end(plan, 5, st);
+    stage_begin(plan, 6, st);
+    if ((rc = launch_grad(plan, g, scat, T, cw, lam, gpart, bpart, st))) return rc;
+    stage_end(plan, 6, st);
+    stage_begin(plan, 7, st);
+    rc = launch_grad_finish(plan, g, T, S, gpart, bpart, cw, g_rc, g_x, g_z, g_delays, st);
+    stage_end(plan, 7, st);
+    return rc;
 }
 
 int simus_batch_rf(int32_t n_sims, simus_plan *const *plans, const simus_tx *tx,

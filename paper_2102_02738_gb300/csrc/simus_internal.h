@@ -74,6 +74,14 @@ int workspace(simus_plan *plan, size_t bytes, void **ptr);
 int plan_setup_host(const simus_probe *probe, const simus_medium *medium, int32_t n_samples,
                     int32_t path, simus_plan *p);
 void plan_fill_tables(const simus_plan *p, SubElem *sub, float2 *H);
+GreenConst green_const(const simus_probe &pr, const simus_medium &md, int N, int nu, double df,
+                       double q_max);
+
+// RMS pressure field (Eq. 22, Eq. 41-42) on midpoint frequencies (j0 + jj + 1/2) gc.df,
+// jj < nf; wt: workspace [T][nf][N]; ptx2: device [nf] = |P_Tx|^2.
+int launch_pfield(const simus_plan *p, const GreenConst &gc, const simus_tx *tx, int64_t npts,
+                  const float *x, const float *y, const float *z, int nf, int j0, float2 *wt,
+                  const float *ptx2, float dw, float *prms, cudaStream_t st);
 
 // Tracing: events around a stage (no-ops unless profiling is enabled) and the
 // process-wide launch counter.
@@ -105,6 +113,21 @@ struct TcGeom {
 TcGeom tc_geometry(const simus_plan *p, int T, int64_t S);
 int launch_tc(const simus_plan *p, const TcGeom &g, const simus_tx *tx, const simus_scat *sc,
               uint16_t *b1img, float2 *part, int *err, cudaStream_t st);
+
+// Adjoint (gradient) path, FP32.
+struct GradGeom {
+    bool ok;             // T * N <= 2048 and the shared-memory tiles fit
+    int n_qtiles, n_chunks;
+    int64_t chunk_len;
+    size_t smem;
+};
+GradGeom grad_geometry(const simus_plan *p, int T, int64_t S);
+int launch_adjoint_dft(const simus_plan *p, const float *drf, int T, float2 *lam, cudaStream_t st);
+int launch_grad(const simus_plan *p, const GradGeom &g, const simus_scat *sc, int T,
+                const float2 *cw, const float2 *lam, float *gpart, float2 *bpart, cudaStream_t st);
+int launch_grad_finish(const simus_plan *p, const GradGeom &g, int T, int64_t S, const float *gpart,
+                       const float2 *bpart, const float2 *cw, float *g_rc, float *g_x, float *g_z,
+                       float *g_delays, cudaStream_t st);
 
 // Sum partial spectra over chunks and multiply by H: spec[c][k] (c = t * N + e).
 int launch_reduce_spectrum(const simus_plan *p, const float2 *part, int n_chunks, int n_chan,
