@@ -139,7 +139,7 @@ k_grad(const GreenConst gc, const SubElem *__restrict__ sub_g, const float *__re
 #pragma unroll
                 for (int j = 0; j < QB; ++j) {
                     const float q = q0 + (float)j;
-                    const float amp = P.inv_r * ex2_a(-q * gc.att2 * P.rh);
+                    const float amp = gc.h * P.inv_r * ex2_a(-q * gc.att2 * P.rh);
                     float2 g, gx, gz;
                     green_grad_term<NARROW>(gc, P, Q, q, amp, g, gx, gz);
                     G[j].x += g.x; G[j].y += g.y;

@@ -1,4 +1,5 @@
-// k_tc.cu -- batched path on the tcgen05 tensor cores.
+// k_tc.cu -- batched path on the tcgen05 tensor cores: one persistent launch over the
+// work items of any number of simulations.
 //
 // The Green's tile G_e(q, s, e) of a bin q and a tile of 128 scatterers is generated once
 // in FP32 (Eq. 17/20/39/40, sub-element sum of Eq. 33), rounded to FP16 (or BF16) in
@@ -10,18 +11,19 @@
 //       B1 rows 2t+1 = [ Im C_t |  Re C_t ]
 //       D1 columns (2t, 2t+1) = (Re P, Im P)    FP32 in tensor memory
 //   reflection + receive sum (Eq. 30-32)   RF_q[e][t] += sum_s G[s][e] R_s P[s][t]
-//       A^T read from the same tile as an MN-major operand: M = e, K = (s | s) over
-//       the Re G and Im G halves -- no second copy of the tile
+//       A^T read from the same tile as an MN-major operand: M = e (in halves of 128 when
+//       Np > 128), K = (s | s) over the Re G and Im G halves -- no transposed copy
 //       B2 rows 2t   = [ Re P' | -Im P' ],  rows 2t+1 = [ Im P' | Re P' ],  P' = R_s P
-//       D2[bin] columns (2t, 2t+1) = (Re RF, Im RF), accumulated over every scatterer
-//       tile of the work item in tensor memory.
+//       D2[bin][half] columns (2t, 2t+1) = (Re RF, Im RF), accumulated over every
+//       scatterer tile of the work item in tensor memory.
 //
-// One CTA per SM (512 threads, persistent over work items = (tile of QB bins, chunk of
-// scatterer tiles)).  Bins are generated in pairs into two tile buffers so that the
-// per-(scatterer, sub-element) geometry -- double-float distance and phase rate -- is
-// shared by both bins.  Per bin: MMA1 -> read P from tensor memory, scale by R_s, write
-// B2 -> MMA2.  All waits are bounded; on a timeout the CTA records an error code, waits
-// for its own bulk copy, frees its tensor memory and returns.
+// Work: a unit is one (simulation, transmit group); a work item is QB bins x a chunk of
+// scatterer tiles of one unit.  One CTA per SM (512 threads) takes items from a global
+// counter until none are left.  With two tile buffers ("pair"), bins are generated two at
+// a time so that the per-(scatterer, sub-element) geometry -- double-float distance and
+// phase rate -- is shared by both.  Per bin: MMA1 -> read P from tensor memory, scale by
+// R_s, write B2 -> MMA2.  All waits are bounded; on a timeout the CTA records an error
+// code, waits for its own bulk copy, frees its tensor memory and returns.
 #include <algorithm>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -36,6 +38,7 @@ namespace {
 constexpr int kThreads = 512;
 constexpr int kSB = 128;          // scatterers per tile
 constexpr int kMaxWait = 1 << 22; // polls before a wait is declared timed out
+constexpr size_t kHeader = 128;   // mbarriers, tensor-memory slot, flags, item index
 
 template <bool BF16>
 __device__ __forceinline__ uint16_t h16(float v) {
@@ -46,12 +49,20 @@ template <bool BF16>
 __device__ __forceinline__ uint32_t h16x2(float lo, float hi) {
     return (uint32_t)h16<BF16>(lo) | ((uint32_t)h16<BF16>(hi) << 16);
 }
+
+// shared memory a unit needs after the header
+size_t unit_smem(int Np, int nN, int pair, int M) {
+    const size_t a = (size_t)kSB * 2 * Np * 2;
+    return (pair ? 2 : 1) * a + (size_t)nN * 2 * Np * 2 + (size_t)nN * 256 * 2
+         + sizeof(float4) * kSB + sizeof(SubElem) * M;
+}
 }  // namespace
 
-// B1 images: per kept bin, the nN x 2Np K-major operand of the transmit GEMM,
+// B1 images of one unit: per kept bin, the nN x 2Np K-major operand of the transmit GEMM
+// for transmits t0 .. t0 + TG - 1,
 //   row 2t: (Re C, -Im C), row 2t+1: (Im C, Re C), C = W exp(i 2 pi frac(q df dtau)).
 template <bool BF16>
-__global__ void k_tc_weights(int T, int N, int Np, int nN, int nq, int q_lo, double df,
+__global__ void k_tc_weights(int TG, int N, int Np, int nN, int nq, int q_lo, double df,
                              const float *__restrict__ delays, const float *__restrict__ apod,
                              uint16_t *__restrict__ img) {
     const int K = 2 * Np;
@@ -65,7 +76,7 @@ __global__ void k_tc_weights(int T, int N, int Np, int nN, int nq, int q_lo, dou
         int t = n >> 1;
         int e = kk < Np ? kk : kk - Np;
         float v = 0.f;
-        if (t < T && e < N) {
+        if (t < TG && e < N) {
             double ph = (double)(q_lo + k) * ((double)delays[t * N + e] * df);
             ph -= rint(ph);
             float s, c;
@@ -79,55 +90,30 @@ __global__ void k_tc_weights(int T, int N, int Np, int nN, int nq, int q_lo, dou
     }
 }
 
-struct TcParams {
-    GreenConst gc;
-    const SubElem *sub;
-    const float *x, *y, *z, *rc;
-    int64_t S;
-    int T, Np, nN, QB;
-    int n_btiles;          // bin tiles of QB bins
-    int n_chunks;          // scatterer chunks
-    int tiles_per_chunk;   // scatterer tiles (of 128) per chunk
-    int n_items;           // n_btiles * n_chunks
-    const uint16_t *b1img; // [nq][nN * 2Np]
-    float2 *part;          // [n_chunks][T][N][nq]
-    int *err;              // error flag
-};
-
 template <bool HAS_Y, bool BF16, bool NARROW, bool LINEAR>
-__global__ void __launch_bounds__(kThreads, 1) k_tc_rf(const TcParams P) {
+__global__ void __launch_bounds__(kThreads, 1)
+k_tc_rf(const TcUnit *__restrict__ units, int n_units, int64_t n_items, int *counter, int *err) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    const GreenConst &gc = P.gc;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int N = gc.N, nu = gc.nu, M = gc.M, nq = gc.nq;
-    const int Np = P.Np, nN = P.nN, T = P.T, QB = P.QB;
-    const int K1 = 2 * Np;
-    const size_t abytes = (size_t)kSB * K1 * 2;
+    __shared__ TcUnit U;                  // the current item's unit
 
-    // shared-memory carve-up (all offsets multiples of 128 bytes)
-    unsigned char *A0 = smem;                              // bin buffer 0: 128 x K1
-    unsigned char *A1 = A0 + abytes;                       // bin buffer 1
-    unsigned char *B1 = A1 + abytes;                       // nN x K1
-    unsigned char *B2 = B1 + (size_t)nN * K1 * 2;          // nN x 256
-    float4 *sc = reinterpret_cast<float4 *>(B2 + (size_t)nN * 256 * 2);   // [128]
-    SubElem *sub = reinterpret_cast<SubElem *>(sc + kSB);                  // [M]
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sub + M);                // 3 mbarriers
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 3);
-    int *abort_flag = reinterpret_cast<int *>(tslot + 1);
-
-    const uint32_t abuf[2] = {tc::smem_u32(A0), tc::smem_u32(A1)};
-    const uint32_t b1s = tc::smem_u32(B1), b2s = tc::smem_u32(B2);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem);          // 3 mbarriers
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + 24);
+    int *abort_flag = reinterpret_cast<int *>(smem + 28);
+    long long *s_item = reinterpret_cast<long long *>(smem + 32);
+    int *s_unit = reinterpret_cast<int *>(smem + 40);
+    unsigned char *dyn = smem + kHeader;
     const uint32_t mbar_b1 = tc::smem_u32(&bars[0]);
     const uint32_t mbar1 = tc::smem_u32(&bars[1]);
     const uint32_t mbar2 = tc::smem_u32(&bars[2]);
 
-    for (int i = tid; i < M; i += kThreads) sub[i] = P.sub[i];
     if (tid == 0) {
         tc::mbar_init(mbar_b1, 1);
         tc::mbar_init(mbar1, 1);
         tc::mbar_init(mbar2, 1);
         tc::fence_mbar_init();
         *abort_flag = 0;
+        *s_unit = -1;
     }
     if (warp == 0) {
         tc::tmem_alloc(tc::smem_u32(tslot), 512);
@@ -137,41 +123,90 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_rf(const TcParams P) {
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *tslot;
-    const uint32_t idesc1 = tc::idesc_f16(128, nN, BF16);
-    const uint32_t idesc2 = idesc1 | (1u << 15);          // A operand MN-major
-    const uint32_t b1_bytes = (uint32_t)nN * K1 * 2;
 
     uint32_t ph_b1 = 0, ph1 = 0, ph2 = 0;
     bool pending2 = false;     // an MMA2 commit not yet waited for
     bool aborted = false;
     bool b1_inflight = false;  // thread 0: a bulk copy into B1 not yet waited for
+    int cur_unit = -1;
 
     auto wait_all = [&](uint32_t mbar, uint32_t parity) -> bool {
         if (!tc::mbar_wait_bounded(mbar, parity, kMaxWait)) atomicExch(abort_flag, 1);
         __syncthreads();
         return *abort_flag == 0;
     };
-    auto issue_b1 = [&](int k) {
-        if (tid == 0) {
-            tc::mbar_arrive_expect_tx(mbar_b1, b1_bytes);
-            tc::bulk_g2s(b1s, P.b1img + (size_t)k * nN * K1, b1_bytes, mbar_b1);
-            b1_inflight = true;
-        }
-    };
 
-    for (int item = blockIdx.x; item < P.n_items && !aborted; item += gridDim.x) {
-        const int bt = item % P.n_btiles, chunk = item / P.n_btiles;
+    while (!aborted) {
+        // ---- next work item (dynamic: heavier units come first in the item order)
+        if (tid == 0) {
+            long long it = atomicAdd(counter, 1);
+            *s_item = it;
+            if (it < n_items) {
+                int lo = 0, hi = n_units - 1;     // last unit with item0 <= it
+                while (lo < hi) {
+                    int mid = (lo + hi + 1) >> 1;
+                    if (units[mid].item0 <= it) lo = mid; else hi = mid - 1;
+                }
+                *s_unit = lo;
+            }
+        }
+        __syncthreads();
+        const long long item = *s_item;
+        if (item >= n_items) break;
+        const int ui = *s_unit;
+        if (ui != cur_unit) {
+            if (pending2) {   // the previous unit's MMA2 may still read the tile buffers
+                if (!wait_all(mbar2, ph2)) { aborted = true; break; }
+                ph2 ^= 1;
+                pending2 = false;
+            }
+            const int nw = (int)(sizeof(TcUnit) / 4);
+            for (int i = tid; i < nw; i += kThreads)
+                reinterpret_cast<int *>(&U)[i] = reinterpret_cast<const int *>(&units[ui])[i];
+            __syncthreads();
+        }
+        const GreenConst &gc = U.gc;
+        const int N = gc.N, nu = gc.nu, M = gc.M, nq = gc.nq;
+        const int Np = U.Np, nN = U.nN, TG = U.TG, QB = U.QB, mh = U.mh, pair = U.pair;
+        const int K1 = 2 * Np;
+        const size_t abytes = (size_t)kSB * K1 * 2;
+        unsigned char *A0 = dyn;
+        unsigned char *A1 = A0 + (pair ? abytes : 0);
+        unsigned char *B1 = A0 + (pair ? 2 : 1) * abytes;
+        unsigned char *B2 = B1 + (size_t)nN * K1 * 2;
+        float4 *sc = reinterpret_cast<float4 *>(B2 + (size_t)nN * 256 * 2);
+        SubElem *sub = reinterpret_cast<SubElem *>(sc + kSB);
+        const uint32_t abuf0 = tc::smem_u32(A0), abuf1 = tc::smem_u32(A1);
+        const uint32_t b1s = tc::smem_u32(B1), b2s = tc::smem_u32(B2);
+        const uint32_t idesc1 = tc::idesc_f16(128, nN, BF16);
+        const uint32_t idesc2 = idesc1 | (1u << 15);          // A operand MN-major
+        const uint32_t b1_bytes = (uint32_t)nN * K1 * 2;
+        if (ui != cur_unit) {
+            for (int i = tid; i < M; i += kThreads) sub[i] = U.sub[i];
+            cur_unit = ui;
+            __syncthreads();
+        }
+        auto issue_b1 = [&](int k) {
+            if (tid == 0) {
+                tc::mbar_arrive_expect_tx(mbar_b1, b1_bytes);
+                tc::bulk_g2s(b1s, U.b1img + (size_t)k * nN * K1, b1_bytes, mbar_b1);
+                b1_inflight = true;
+            }
+        };
+
+        const int64_t li = item - U.item0;
+        const int bt = (int)(li % U.n_btiles), chunk = (int)(li / U.n_btiles);
         const int k0 = bt * QB;
-        const int64_t tile0 = (int64_t)chunk * P.tiles_per_chunk;
-        const int64_t n_tiles_total = (P.S + kSB - 1) / kSB;
-        const int64_t tile1 = std::min<int64_t>(tile0 + P.tiles_per_chunk, n_tiles_total);
+        const int64_t tile0 = (int64_t)chunk * U.tiles_per_chunk;
+        const int64_t tile1 = std::min<int64_t>(tile0 + U.tiles_per_chunk, U.n_tiles);
+        const int step = pair ? 2 : 1;
         for (int64_t tile = tile0; tile < tile1 && !aborted; ++tile) {
-            for (int bp = 0; bp < QB && !aborted; bp += 2) {
-                const int nb = min(2, QB - bp);
+            for (int bp = 0; bp < QB && !aborted; bp += step) {
+                const int nb = min(step, QB - bp);
                 const int kA = min(k0 + bp, nq - 1);       // bins past the end repeat the last
                 const int kB = min(k0 + bp + 1, nq - 1);   // (their outputs are discarded)
                 issue_b1(kA);
-                if (pending2) {   // both tile buffers and B2 still read by the last MMA2
+                if (pending2) {   // tile buffers and B2 still read by the last MMA2
                     if (!wait_all(mbar2, ph2)) { aborted = true; break; }
                     ph2 ^= 1;
                     pending2 = false;
@@ -179,12 +214,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_rf(const TcParams P) {
                 if (bp == 0) {    // new scatterer tile
                     for (int i = tid; i < kSB; i += kThreads) {
                         int64_t s = tile * kSB + i;
-                        sc[i] = s < P.S ? make_float4(P.x[s], HAS_Y ? P.y[s] : 0.f, P.z[s], P.rc[s])
+                        sc[i] = s < U.S ? make_float4(U.x[s], (HAS_Y && U.y) ? U.y[s] : 0.f, U.z[s], U.rc[s])
                                         : make_float4(0.f, 0.f, 1.f, 0.f);
                     }
                     __syncthreads();
                 }
-                // ---- Green's tiles of bins kA (buffer 0) and kB (buffer 1): items (s, 8 elements)
+                // ---- Green's tiles of bin kA (buffer 0) and kB (buffer 1): items (s, 8 elements)
                 const float qA = (float)(gc.q_lo + kA), qB = (float)(gc.q_lo + kB);
                 const int n_groups = Np >> 3;
                 for (int it = tid; it < kSB * n_groups; it += kThreads) {
@@ -232,7 +267,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_rf(const TcParams P) {
                 tc::fence_after_sync();
 
                 for (int bi_ = 0; bi_ < nb && !aborted; ++bi_) {
-                    const uint32_t abase = abuf[bi_];
+                    const uint32_t abase = bi_ ? abuf1 : abuf0;
                     // ---- MMA1: D1 = A * B1^T
                     if (tid == 0) {
                         if (!tc::mbar_wait_bounded(mbar_b1, ph_b1, kMaxWait)) {
@@ -270,7 +305,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_rf(const TcParams P) {
                             for (int i = 0; i < 8; ++i) {
                                 const int t = (c0 >> 1) + i;
                                 float pr = 0.f, pi = 0.f;
-                                if (t < T) { pr = R * v[2 * i]; pi = R * v[2 * i + 1]; }
+                                if (t < TG) { pr = R * v[2 * i]; pi = R * v[2 * i + 1]; }
                                 const int n0 = 2 * t;
                                 *reinterpret_cast<uint16_t *>(B2 + tc::kmajor_offset(n0, s, 256)) = h16<BF16>(pr);
                                 *reinterpret_cast<uint16_t *>(B2 + tc::kmajor_offset(n0, 128 + s, 256)) = h16<BF16>(-pi);
@@ -283,20 +318,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_rf(const TcParams P) {
                     tc::fence_before_sync();
                     __syncthreads();
                     tc::fence_after_sync();
-                    // ---- MMA2: D2[bin] (+)= A^T * B2^T, A^T the MN-major view of the tile:
-                    // k-slice j covers scatterers 16 (j mod 8) .. +15 of the Re (j < 8) or
-                    // Im (j >= 8) half.  In the no-swizzle MN-major form the leading byte
-                    // offset is the stride between K-adjacent core matrices (scatterer
-                    // groups, 16 K1 bytes) and the stride byte offset the one between
-                    // MN-adjacent core matrices (element groups, 128 bytes).
+                    // ---- MMA2: D2[bin][half] (+)= A^T * B2^T, A^T the MN-major view of
+                    // the tile: k-slice j covers scatterers 16 (j mod 8) .. +15 of the Re
+                    // (j < 8) or Im (j >= 8) half.  In the no-swizzle MN-major form the
+                    // leading byte offset is the stride between K-adjacent core matrices
+                    // (scatterer groups, 16 K1 bytes) and the stride byte offset the one
+                    // between MN-adjacent core matrices (element groups, 128 bytes).
                     if (tid == 0) {
-                        const uint32_t d2 = tmem + (uint32_t)(nN * (1 + bp + bi_));
-                        for (int j = 0; j < 16; ++j) {
-                            const uint32_t a0 = abase + (uint32_t)((2 * (j & 7)) * 16 * K1)
-                                              + (uint32_t)((j >> 3) * (Np / 8) * 128);
-                            uint64_t ad = tc::smem_desc(a0, 16 * K1, 128);
-                            uint64_t bd = tc::smem_desc(b2s + 256 * j, 128, 4096);
-                            tc::mma_f16(d2, ad, bd, idesc2, (j > 0 || tile > tile0) ? 1u : 0u);
+                        for (int h = 0; h < mh; ++h) {
+                            const uint32_t d2 = tmem + (uint32_t)(nN * (1 + (bp + bi_) * mh + h));
+                            for (int j = 0; j < 16; ++j) {
+                                const uint32_t a0 = abase + (uint32_t)((2 * (j & 7)) * 16 * K1)
+                                                  + (uint32_t)((j >> 3) * (Np / 8) * 128) + (uint32_t)(h * 16 * 128);
+                                uint64_t ad = tc::smem_desc(a0, 16 * K1, 128);
+                                uint64_t bd = tc::smem_desc(b2s + 256 * j, 128, 4096);
+                                tc::mma_f16(d2, ad, bd, idesc2, (j > 0 || tile > tile0) ? 1u : 0u);
+                            }
                         }
                         tc::mma_commit(mbar2);
                     }
@@ -311,22 +348,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_rf(const TcParams P) {
             pending2 = false;
         }
         tc::fence_after_sync();
-        // ---- partial spectra of this item: part[chunk][t][e][k]
+        // ---- partial spectra of this item: part[chunk][t0 + t][e][k]
         {
             const int sp = warp & 3, cc = warp >> 2;
-            const int e = sp * 32 + lane;
             for (int b = 0; b < QB; ++b) {
                 const int k = k0 + b;
-                for (int c0 = cc * 16; c0 < nN; c0 += 64) {
-                    float v[16];
-                    tc::tmem_ld16(tmem + ((uint32_t)(sp * 32) << 16) + (uint32_t)(nN * (1 + b) + c0), v);
-                    if (k < nq && e < N) {
+                for (int h = 0; h < mh; ++h) {
+                    const int e = 128 * h + sp * 32 + lane;
+                    for (int c0 = cc * 16; c0 < nN; c0 += 64) {
+                        float v[16];
+                        tc::tmem_ld16(tmem + ((uint32_t)(sp * 32) << 16) +
+                                          (uint32_t)(nN * (1 + b * mh + h) + c0), v);
+                        if (k < nq && e < N) {
 #pragma unroll
-                        for (int i = 0; i < 8; ++i) {
-                            const int t = (c0 >> 1) + i;
-                            if (t < T)
-                                P.part[(((size_t)chunk * T + t) * N + e) * nq + k] =
-                                    make_float2(v[2 * i], v[2 * i + 1]);
+                            for (int i = 0; i < 8; ++i) {
+                                const int t = (c0 >> 1) + i;
+                                if (t < TG)
+                                    U.part[(((size_t)chunk * U.T + U.t0 + t) * N + e) * nq + k] =
+                                        make_float2(v[2 * i], v[2 * i + 1]);
+                            }
                         }
                     }
                 }
@@ -337,7 +377,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_rf(const TcParams P) {
         tc::fence_after_sync();
     }
     if (*abort_flag && tid == 0) {
-        atomicExch(P.err, SIMUS_ERR_TIMEOUT);
+        atomicExch(err, SIMUS_ERR_TIMEOUT);
         if (b1_inflight) tc::mbar_wait_bounded(mbar_b1, ph_b1, kMaxWait);   // own copy in flight
     }
     tc::fence_before_sync();
@@ -345,28 +385,44 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_rf(const TcParams P) {
     if (warp == 0) tc::tmem_dealloc(tmem, 512);
 }
 
-TcGeom tc_geometry(const simus_plan *p, int T, int64_t S) {
-    TcGeom g{};
+// Shape of one simulation on this kernel.  Transmit groups as large as the tensor
+// memory (512 columns: D1 + QB * mh D2 slices of nN columns) and shared memory allow;
+// two tile buffers when they fit; chunk sizes from the simulation's share of the work.
+TcShape tc_shape(const simus_plan *p, int T, int64_t S, double work_share, int items_per_sm) {
+    TcShape g{};
     g.Np = (p->N + 7) & ~7;
-    g.nN = ((2 * T + 15) / 16) * 16;
-    g.ok = p->N <= 128 && g.nN <= 256;
+    if (g.Np > 256) return g;
+    g.mh = g.Np > 128 ? 2 : 1;
+    const size_t limit = 227 * 1024 - kHeader - 1024;
+    for (int TG = std::min(T, 120); TG >= 1; TG = (TG > 8 ? TG - 8 : TG - 1)) {
+        const int nN = ((2 * TG + 15) / 16) * 16;
+        const int qb = (512 - nN) / (nN * g.mh);
+        if (qb < 1) continue;
+        for (int pair = 1; pair >= 0; --pair) {
+            if (pair && qb < 2) continue;
+            const size_t sm = unit_smem(g.Np, nN, pair, p->M);
+            if (sm <= limit) {
+                g.ok = true;
+                g.TG = TG; g.nN = nN; g.pair = pair;
+                g.QB = std::min(4, qb);
+                if (pair && (g.QB & 1)) g.QB -= 1;
+                g.smem = sm + kHeader;
+                break;
+            }
+        }
+        if (g.ok) break;
+    }
     if (!g.ok) return g;
-    g.QB = std::max(1, std::min(4, (512 - g.nN) / g.nN));
-    if (g.QB == 3) g.QB = 2;   // bins go in pairs
+    g.n_groups = (T + g.TG - 1) / g.TG;
     g.n_btiles = (p->nq + g.QB - 1) / g.QB;
-    const int64_t n_tiles = std::max<int64_t>(1, (S + kSB - 1) / kSB);
-    // chunks: enough items for ~4 per SM, chunks of at least 4 scatterer tiles
-    int64_t want_items = (int64_t)p->num_sms * 4;
-    int64_t chunks = std::max<int64_t>(1, want_items / g.n_btiles);
-    chunks = std::min<int64_t>(chunks, std::max<int64_t>(1, n_tiles / 4));
-    g.tiles_per_chunk = (int)((n_tiles + chunks - 1) / chunks);
-    g.n_chunks = (int)((n_tiles + g.tiles_per_chunk - 1) / g.tiles_per_chunk);
-    g.n_items = g.n_btiles * g.n_chunks;
-    g.grid = (int)std::min<int64_t>(g.n_items, p->num_sms);
+    g.n_tiles = std::max<int64_t>(1, (S + kSB - 1) / kSB);
+    // chunks: this simulation's share of ~items_per_sm items per SM
+    const double want = std::max(1.0, work_share * items_per_sm * p->num_sms);
+    int64_t chunks = (int64_t)std::ceil(want / ((double)g.n_btiles * g.n_groups));
+    chunks = std::max<int64_t>(1, std::min<int64_t>(chunks, std::max<int64_t>(1, g.n_tiles / 2)));
+    g.tiles_per_chunk = (int)((g.n_tiles + chunks - 1) / chunks);
+    g.n_chunks = (int)((g.n_tiles + g.tiles_per_chunk - 1) / g.tiles_per_chunk);
     g.b1_bytes = (size_t)p->nq * g.nN * 2 * g.Np * 2;
-    g.smem = 2 * (size_t)kSB * 2 * g.Np * 2 + (size_t)g.nN * 2 * g.Np * 2
-           + (size_t)g.nN * 256 * 2 + sizeof(float4) * kSB + sizeof(SubElem) * p->M + 64;
-    g.ok = g.smem <= 227 * 1024;
     return g;
 }
 
@@ -376,37 +432,30 @@ static auto pick_tc(bool narrow, bool linear) {
                   : (linear ? k_tc_rf<HAS_Y, BF16, false, true> : k_tc_rf<HAS_Y, BF16, false, false>);
 }
 
-int launch_tc(const simus_plan *p, const TcGeom &g, const simus_tx *tx, const simus_scat *sc,
-              uint16_t *b1img, float2 *part, int *err, cudaStream_t st) {
-    const bool bf16 = p->path == SIMUS_PATH_TC_BF16;
-    {
-        int64_t total = (int64_t)p->nq * g.nN * 2 * g.Np;
-        int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)p->num_sms * 16);
+int launch_tc_units(const TcUnit *h_units, const TcUnit *d_units, int n_units, int64_t n_items,
+                    size_t smem, bool bf16, bool has_y, bool narrow, bool linear, int num_sms,
+                    int *counter, int *err, cudaStream_t st) {
+    for (int u = 0; u < n_units; ++u) {
+        const TcUnit &U = h_units[u];
+        int64_t total = (int64_t)U.gc.nq * U.nN * 2 * U.Np;
+        int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)num_sms * 16);
+        const float *dl = U.delays + (size_t)U.t0 * U.gc.N, *ap = U.apod + (size_t)U.t0 * U.gc.N;
         if (bf16)
-            k_tc_weights<true><<<blocks, 256, 0, st>>>(tx->n_tx, p->N, g.Np, g.nN, p->nq, p->q_lo,
-                                                       p->gc.df, tx->delays, tx->apod, b1img);
+            k_tc_weights<true><<<blocks, 256, 0, st>>>(U.TG, U.gc.N, U.Np, U.nN, U.gc.nq, U.gc.q_lo,
+                                                       U.gc.df, dl, ap, U.b1img);
         else
-            k_tc_weights<false><<<blocks, 256, 0, st>>>(tx->n_tx, p->N, g.Np, g.nN, p->nq, p->q_lo,
-                                                        p->gc.df, tx->delays, tx->apod, b1img);
+            k_tc_weights<false><<<blocks, 256, 0, st>>>(U.TG, U.gc.N, U.Np, U.nN, U.gc.nq, U.gc.q_lo,
+                                                        U.gc.df, dl, ap, U.b1img);
         count_launches(1);
         int rc = check_cuda(cudaGetLastError(), "k_tc_weights launch");
         if (rc) return rc;
     }
-    TcParams P;
-    P.gc = p->gc;
-    P.sub = p->d_sub;
-    P.x = sc->x; P.y = sc->y; P.z = sc->z; P.rc = sc->rc;
-    P.S = sc->n;
-    P.T = tx->n_tx; P.Np = g.Np; P.nN = g.nN; P.QB = g.QB;
-    P.n_btiles = g.n_btiles; P.n_chunks = g.n_chunks; P.tiles_per_chunk = g.tiles_per_chunk;
-    P.n_items = g.n_items;
-    P.b1img = b1img; P.part = part; P.err = err;
-    const bool has_y = sc->y != nullptr, narrow = p->gc.narrow != 0, linear = p->probe.radius <= 0;
     auto kern = has_y ? (bf16 ? pick_tc<true, true>(narrow, linear) : pick_tc<true, false>(narrow, linear))
                       : (bf16 ? pick_tc<false, true>(narrow, linear) : pick_tc<false, false>(narrow, linear));
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return check_cuda(e, "k_tc_rf smem attribute");
-    kern<<<g.grid, kThreads, g.smem, st>>>(P);
+    const int grid = (int)std::min<int64_t>(n_items, num_sms);
+    kern<<<grid, kThreads, smem, st>>>(d_units, n_units, n_items, counter, err);
     count_launches(1);
     return check_cuda(cudaGetLastError(), "k_tc_rf launch");
 }

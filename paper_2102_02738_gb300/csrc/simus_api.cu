@@ -19,12 +19,6 @@ namespace {
 thread_local char g_err[512] = "";
 std::atomic<int64_t> g_launches{0};
 
-// Eq. 18: four-Gaussian approximation of the rectangle (third and fourth conjugates).
-const double kAre[4] = {0.187, 0.288, 0.187, 0.288};
-const double kAim[4] = {0.275, -1.954, -0.275, 1.954};
-const double kBre[4] = {4.558, 8.598, 4.558, 8.598};
-const double kBim[4] = {-25.59, -7.924, 25.59, 7.924};
-
 inline double sinc_d(double x) { return x == 0.0 ? 1.0 : std::sin(x) / x; }
 
 // Eq. 26-27: two-way transducer response.
@@ -78,8 +72,25 @@ int resolve_nsub(const simus_probe &pr, const simus_medium &md) {
     return std::max(1, (int)std::ceil(pr.width / lambda_min));
 }
 
+// True while the calling thread's current entry point enqueues on a capturing stream:
+// then only capture-safe CUDA calls are made (no pointer queries, no event queries).
+thread_local bool g_capturing = false;
+
+void note_capture(void *stream) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    g_capturing = cudaStreamIsCapturing(reinterpret_cast<cudaStream_t>(stream), &cs) == cudaSuccess &&
+                  cs != cudaStreamCaptureStatusNone;
+}
+
+// Sets the flag for the duration of one entry point.
+struct CaptureScope {
+    explicit CaptureScope(void *stream) { note_capture(stream); }
+    ~CaptureScope() { g_capturing = false; }
+};
+
 int check_device_ptr(const void *ptr, const char *name, bool allow_null = false) {
     if (!ptr) return allow_null ? SIMUS_OK : fail(SIMUS_ERR_ARG, "%s must not be NULL", name);
+    if (g_capturing) return SIMUS_OK;
     cudaPointerAttributes a{};
     cudaError_t e = cudaPointerGetAttributes(&a, ptr);
     if (e != cudaSuccess) {
@@ -152,6 +163,8 @@ void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed);
 
 int workspace(simus_plan *plan, size_t bytes, void **ptr) {
     if (bytes > plan->work_bytes) {
+        if (g_capturing)
+            return fail(SIMUS_ERR_ARG, "workspace must grow: make a warm-up call before stream capture");
         if (plan->d_work) {
             cudaError_t e = cudaDeviceSynchronize();
             if (e != cudaSuccess) return check_cuda(e, "workspace sync");
@@ -237,14 +250,8 @@ GreenConst green_const(const simus_probe &pr, const simus_medium &md, int N, int
     // Eq. 40: k_a = alpha_dB / 8.69 * f * 1e-4 per metre; base 2 per bin.
     gc.att2 = (float)(medium->alpha_db / 8.69 * df * 1e-4 / std::log(2.0));
     gc.zeta = (float)probe->zeta;
-    const double h2 = probe->height * probe->height;
-    for (int g = 0; g < 4; ++g) {
-        gc.ga[g] = (float)(kBre[g] / h2);
-        gc.gb[g] = (float)(kBim[g] / h2);
-        gc.ga2[g] = (float)((kBre[g] / h2) * (kBre[g] / h2));
-        gc.Cr[g] = (float)(kAre[g] * std::sqrt(M_PI / 2.0));
-        gc.Ci[g] = (float)(kAim[g] * std::sqrt(M_PI / 2.0));
-    }
+    gc.h = (float)probe->height;
+    gc.h2 = (float)(probe->height * probe->height);
     gc.narrow = (2.0 * M_PI * K * b / nu) * q_max <= 3.19 ? 1 : 0;
     gc.df = df;
     return gc;
@@ -355,6 +362,8 @@ void simus_plan_destroy(simus_plan *plan) {
     cudaDeviceSynchronize();
     for (auto &e : plan->ev)
         if (e) cudaEventDestroy(e);
+    if (plan->ev_stage) cudaEventDestroy(plan->ev_stage);
+    if (plan->h_stage) cudaFreeHost(plan->h_stage);
     cudaFree(plan->d_sub);
     cudaFree(plan->d_H);
     cudaFree(plan->d_err);
@@ -426,61 +435,202 @@ int simus_plan_get_info(const simus_plan *plan, simus_plan_info *info) {
 namespace {
 
 // Workspace layout of one RF call: [weights | partial spectra | spectrum (simus_rf)].
-struct CallLayout {
-    bool tc;
-    PlainGeom pg;
-    TcGeom tg;
-    int n_chunks;
-    size_t w_bytes, part_bytes, spec_bytes;
-    size_t total() const { return w_bytes + part_bytes + spec_bytes; }
-};
-
-int call_layout(const simus_plan *p, int T, int64_t S, bool with_spec, CallLayout &L) {
-    const int n_chan = T * p->N;
-    L = CallLayout{};
-    L.tc = p->path != SIMUS_PATH_PLAIN_F32;
-    if (L.tc) {
-        L.tg = tc_geometry(p, T, S);
-        if (!L.tg.ok)
-            return fail(SIMUS_ERR_UNSUPPORTED,
-                        "tensor-core path needs N <= 128 and 2T <= 256 (N=%d, T=%d)", p->N, T);
-        L.n_chunks = L.tg.n_chunks;
-        L.w_bytes = align256(L.tg.b1_bytes);
-    } else {
-        L.pg = plain_geometry(p, T, S);
-        L.n_chunks = L.pg.n_chunks;
-        L.w_bytes = align256(sizeof(float2) * (size_t)T * p->nq * p->N);
-    }
-    L.part_bytes = align256(sizeof(float2) * (size_t)L.n_chunks * n_chan * p->nq);
-    L.spec_bytes = with_spec ? align256(sizeof(float2) * (size_t)n_chan * p->nq) : 0;
-    return SIMUS_OK;
+// Plain FP32 path of one simulation in p's workspace [weights | partials | spectrum]:
+// the spectrum goes to spec_out if given (else to the workspace), the time signals to rf
+// if given.
+int plain_run(simus_plan *p, const simus_tx *tx, const simus_scat *sc, float2 *spec_out,
+              float *rf, cudaStream_t st) {
+    const int T = tx->n_tx, n_chan = T * p->N;
+    const PlainGeom g = plain_geometry(p, T, sc->n);
+    const size_t w_b = align256(sizeof(float2) * (size_t)T * p->nq * p->N);
+    const size_t part_b = align256(sizeof(float2) * (size_t)g.n_chunks * n_chan * p->nq);
+    const size_t spec_b = spec_out ? 0 : align256(sizeof(float2) * (size_t)n_chan * p->nq);
+    void *ws;
+    int rc;
+    if ((rc = workspace(p, w_b + part_b + spec_b, &ws))) return rc;
+    char *base = reinterpret_cast<char *>(ws);
+    float2 *cw = reinterpret_cast<float2 *>(base);
+    float2 *part = reinterpret_cast<float2 *>(base + w_b);
+    float2 *spec = spec_out ? spec_out : reinterpret_cast<float2 *>(base + w_b + part_b);
+    stage_begin(p, 0, st);
+    if ((rc = launch_tx_weights(p, tx, cw, st))) return rc;
+    stage_end(p, 0, st);
+    stage_begin(p, 1, st);
+    if ((rc = launch_plain(p, g, sc, T, cw, part, st))) return rc;
+    stage_end(p, 1, st);
+    stage_begin(p, 2, st);
+    if ((rc = launch_reduce_spectrum(p, part, g.n_chunks, n_chan, spec, st))) return rc;
+    stage_end(p, 2, st);
+    if (!rf) return SIMUS_OK;
+    stage_begin(p, 3, st);
+    rc = launch_idft(p, spec, n_chan, rf, st);
+    stage_end(p, 3, st);
+    return rc;
 }
 
-// Spectrum X[t][e][k] (with transfer factor) into `spec`, workspace per `L` at `ws`.
-int rf_spectrum_run(simus_plan *p, const CallLayout &L, void *ws, const simus_tx *tx,
-                    const simus_scat *sc, float2 *spec, cudaStream_t st) {
-    const int T = tx->n_tx, n_chan = T * p->N;
-    char *base = reinterpret_cast<char *>(ws);
-    float2 *part = reinterpret_cast<float2 *>(base + L.w_bytes);
-    int rc;
-    if (L.tc) {
-        stage_begin(p, 1, st);
-        rc = launch_tc(p, L.tg, tx, sc, reinterpret_cast<uint16_t *>(base), part, p->d_err, st);
-        stage_end(p, 1, st);
-        if (rc) return rc;
-    } else {
-        float2 *cw = reinterpret_cast<float2 *>(base);
-        stage_begin(p, 0, st);
-        if ((rc = launch_tx_weights(p, tx, cw, st))) return rc;
-        stage_end(p, 0, st);
-        stage_begin(p, 1, st);
-        if ((rc = launch_plain(p, L.pg, sc, T, cw, part, st))) return rc;
-        stage_end(p, 1, st);
+// Tensor-core path of n simulations in one persistent launch; temporaries in owner's
+// workspace [unit descriptors | work counter | B1 images | partials | spectra].  Each
+// simulation's spectrum goes to specs[i] if given, its time signals to rfs[i] if given.
+// Simulations with no scatterer get zero outputs.
+int tc_execute(simus_plan *owner, int n, simus_plan *const *plans, const simus_tx *txs,
+               const simus_scat *scs, float2 *const *specs, float *const *rfs, cudaStream_t st) {
+    std::vector<int> live;
+    double total = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const simus_plan *p = plans[i];
+        const int n_chan = txs[i].n_tx * p->N;
+        if (scs[i].n == 0) {
+            int rc = specs && specs[i]
+                ? check_cuda(cudaMemsetAsync(specs[i], 0, sizeof(float2) * (size_t)n_chan * p->nq, st), "memset")
+                : SIMUS_OK;
+            if (!rc && rfs && rfs[i])
+                rc = check_cuda(cudaMemsetAsync(rfs[i], 0, sizeof(float) * (size_t)n_chan * p->nt, st), "memset");
+            if (rc) return rc;
+            continue;
+        }
+        live.push_back(i);
+        total += (double)p->nq * (double)scs[i].n * p->M * txs[i].n_tx;
     }
-    stage_begin(p, 2, st);
-    rc = launch_reduce_spectrum(p, part, L.n_chunks, n_chan, spec, st);
-    stage_end(p, 2, st);
-    return rc;
+    if (live.empty()) return SIMUS_OK;
+    const int nl = (int)live.size();
+    std::vector<TcShape> sh(nl);
+    size_t smem = 0;
+    int n_units = 0;
+    bool has_y = false, narrow = true, linear = true;
+    for (int j = 0; j < nl; ++j) {
+        const int i = live[j];
+        const simus_plan *p = plans[i];
+        const double w = (double)p->nq * (double)scs[i].n * p->M * txs[i].n_tx / total;
+        sh[j] = tc_shape(p, txs[i].n_tx, scs[i].n, w, owner->items_per_sm);
+        if (!sh[j].ok)
+            return fail(SIMUS_ERR_UNSUPPORTED, "tensor-core path: simulation %d (N=%d, nu=%d) does not fit",
+                        i, p->N, p->nu);
+        smem = std::max(smem, sh[j].smem);
+        n_units += sh[j].n_groups;
+        has_y = has_y || scs[i].y != nullptr;
+        narrow = narrow && p->gc.narrow;
+        linear = linear && p->probe.radius <= 0;
+    }
+    // workspace
+    const size_t units_b = align256(sizeof(TcUnit) * n_units);
+    size_t off = units_b + 256;
+    std::vector<size_t> b1_off(n_units), part_off(nl), spec_off(nl);
+    {
+        int u = 0;
+        for (int j = 0; j < nl; ++j)
+            for (int g = 0; g < sh[j].n_groups; ++g, ++u) { b1_off[u] = off; off += align256(sh[j].b1_bytes); }
+        for (int j = 0; j < nl; ++j) {
+            const simus_plan *p = plans[live[j]];
+            part_off[j] = off;
+            off += align256(sizeof(float2) * (size_t)sh[j].n_chunks * txs[live[j]].n_tx * p->N * p->nq);
+        }
+        for (int j = 0; j < nl; ++j) {
+            const simus_plan *p = plans[live[j]];
+            spec_off[j] = off;
+            if (!(specs && specs[live[j]])) off += align256(sizeof(float2) * (size_t)txs[live[j]].n_tx * p->N * p->nq);
+        }
+    }
+    void *ws;
+    int rc;
+    if ((rc = workspace(owner, off, &ws))) return rc;
+    char *base = reinterpret_cast<char *>(ws);
+    TcUnit *d_units = reinterpret_cast<TcUnit *>(base);
+    int *counter = reinterpret_cast<int *>(base + units_b);
+
+    // unit descriptors in pinned staging (the previous call's copy must have read it)
+    const size_t need = sizeof(TcUnit) * n_units;
+    // While capturing, the caller has completed the previous (warm-up) call before
+    // starting the capture, so the staging buffer is free.
+    if (owner->stage_pending && g_capturing) owner->stage_pending = false;
+    if (owner->stage_pending) {   // query first: a completed copy needs no wait
+        if (cudaEventQuery(owner->ev_stage) != cudaSuccess &&
+            (rc = check_cuda(cudaEventSynchronize(owner->ev_stage), "staging event")))
+            return rc;
+        owner->stage_pending = false;
+    }
+    if (need > owner->h_stage_bytes) {
+        if (g_capturing)
+            return fail(SIMUS_ERR_ARG, "stream capture needs a completed warm-up call of the same batch first");
+        if (owner->h_stage) cudaFreeHost(owner->h_stage);
+        owner->h_stage = nullptr;
+        owner->h_stage_bytes = 0;
+        if ((rc = check_cuda(cudaMallocHost(&owner->h_stage, need * 2), "pinned staging"))) return rc;
+        owner->h_stage_bytes = need * 2;
+    }
+    if (!owner->ev_stage &&
+        (rc = check_cuda(cudaEventCreateWithFlags(&owner->ev_stage, cudaEventDisableTiming), "event")))
+        return rc;
+    TcUnit *hu = reinterpret_cast<TcUnit *>(owner->h_stage);
+    std::vector<std::pair<double, int>> order;
+    {
+        int u = 0;
+        for (int j = 0; j < nl; ++j) {
+            const int i = live[j];
+            const simus_plan *p = plans[i];
+            const TcShape &s = sh[j];
+            for (int g = 0; g < s.n_groups; ++g, ++u) {
+                TcUnit U{};
+                U.gc = p->gc;
+                U.sub = p->d_sub;
+                U.x = scs[i].x; U.y = scs[i].y; U.z = scs[i].z; U.rc = scs[i].rc;
+                U.delays = txs[i].delays; U.apod = txs[i].apod;
+                U.S = scs[i].n; U.n_tiles = s.n_tiles;
+                U.T = txs[i].n_tx; U.t0 = g * s.TG; U.TG = std::min(s.TG, U.T - U.t0);
+                U.Np = s.Np; U.mh = s.mh; U.pair = s.pair; U.QB = s.QB;
+                U.nN = ((2 * U.TG + 15) / 16) * 16;
+                U.n_btiles = s.n_btiles; U.n_chunks = s.n_chunks; U.tiles_per_chunk = s.tiles_per_chunk;
+                U.b1img = reinterpret_cast<uint16_t *>(base + b1_off[u]);
+                U.part = reinterpret_cast<float2 *>(base + part_off[j]);
+                hu[u] = U;
+                order.push_back({(double)s.QB * s.tiles_per_chunk * s.Np * p->nu, u});
+            }
+        }
+    }
+    // heaviest items first; item0 = prefix of item counts in that order
+    std::stable_sort(order.begin(), order.end(), [](auto &a, auto &b) { return a.first > b.first; });
+    std::vector<TcUnit> sorted(n_units);
+    int64_t n_items = 0;
+    for (int k = 0; k < n_units; ++k) {
+        sorted[k] = hu[order[k].second];
+        sorted[k].item0 = n_items;
+        n_items += (int64_t)sorted[k].n_btiles * sorted[k].n_chunks;
+    }
+    std::copy(sorted.begin(), sorted.end(), hu);
+    if ((rc = check_cuda(cudaMemcpyAsync(d_units, hu, need, cudaMemcpyHostToDevice, st), "upload units"))) return rc;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st, &cs);
+    if (cs == cudaStreamCaptureStatusNone) {
+        if ((rc = check_cuda(cudaEventRecord(owner->ev_stage, st), "staging event"))) return rc;
+        owner->stage_pending = true;
+    }
+    if ((rc = check_cuda(cudaMemsetAsync(counter, 0, sizeof(int), st), "memset counter"))) return rc;
+    stage_begin(owner, 1, st);
+    rc = launch_tc_units(hu, d_units, n_units, n_items, smem, owner->path == SIMUS_PATH_TC_BF16, has_y,
+                         narrow, linear, owner->num_sms, counter, owner->d_err, st);
+    stage_end(owner, 1, st);
+    if (rc) return rc;
+    stage_begin(owner, 2, st);
+    for (int j = 0; j < nl; ++j) {
+        const int i = live[j];
+        simus_plan *p = plans[i];
+        const int n_chan = txs[i].n_tx * p->N;
+        float2 *spec = specs && specs[i] ? specs[i] : reinterpret_cast<float2 *>(base + spec_off[j]);
+        if ((rc = launch_reduce_spectrum(p, reinterpret_cast<float2 *>(base + part_off[j]), sh[j].n_chunks,
+                                         n_chan, spec, st)))
+            return rc;
+    }
+    stage_end(owner, 2, st);
+    if (!rfs) return SIMUS_OK;
+    stage_begin(owner, 3, st);
+    for (int j = 0; j < nl; ++j) {
+        const int i = live[j];
+        if (!rfs[i]) continue;
+        simus_plan *p = plans[i];
+        float2 *spec = specs && specs[i] ? specs[i] : reinterpret_cast<float2 *>(base + spec_off[j]);
+        if ((rc = launch_idft(p, spec, txs[i].n_tx * p->N, rfs[i], st))) return rc;
+    }
+    stage_end(owner, 3, st);
+    return SIMUS_OK;
 }
 
 }  // namespace
@@ -489,6 +639,7 @@ extern "C" {
 
 int simus_rf_spectrum(simus_plan *plan, const simus_tx *tx, const simus_scat *scat, float *spec,
                       void *stream) {
+    CaptureScope capture_scope(stream);
     if (!plan) return fail(SIMUS_ERR_ARG, "plan must not be NULL");
     for (bool &u : plan->stage_used) u = false;
     int rc;
@@ -500,15 +651,14 @@ int simus_rf_spectrum(simus_plan *plan, const simus_tx *tx, const simus_scat *sc
     if (scat->n == 0)
         return check_cuda(cudaMemsetAsync(spec, 0, sizeof(float2) * (size_t)tx->n_tx * plan->N * plan->nq, st),
                           "memset spectrum");
-    CallLayout L;
-    if ((rc = call_layout(plan, tx->n_tx, scat->n, false, L))) return rc;
-    void *ws;
-    if ((rc = workspace(plan, L.total(), &ws))) return rc;
-    return rf_spectrum_run(plan, L, ws, tx, scat, reinterpret_cast<float2 *>(spec), st);
+    float2 *sp = reinterpret_cast<float2 *>(spec);
+    if (plan->path == SIMUS_PATH_PLAIN_F32) return plain_run(plan, tx, scat, sp, nullptr, st);
+    return tc_execute(plan, 1, &plan, tx, scat, &sp, nullptr, st);
 }
 
 int simus_rf(simus_plan *plan, const simus_tx *tx, const simus_scat *scat, float *rf,
              void *stream) {
+    CaptureScope capture_scope(stream);
     if (!plan) return fail(SIMUS_ERR_ARG, "plan must not be NULL");
     for (bool &u : plan->stage_used) u = false;
     int rc;
@@ -521,20 +671,13 @@ int simus_rf(simus_plan *plan, const simus_tx *tx, const simus_scat *scat, float
     if (scat->n == 0)
         return check_cuda(cudaMemsetAsync(rf, 0, sizeof(float) * (size_t)n_chan * plan->nt, st),
                           "memset rf");
-    CallLayout L;
-    if ((rc = call_layout(plan, tx->n_tx, scat->n, true, L))) return rc;
-    void *ws;
-    if ((rc = workspace(plan, L.total(), &ws))) return rc;
-    float2 *spec = reinterpret_cast<float2 *>(reinterpret_cast<char *>(ws) + L.w_bytes + L.part_bytes);
-    if ((rc = rf_spectrum_run(plan, L, ws, tx, scat, spec, st))) return rc;
-    stage_begin(plan, 3, st);
-    rc = launch_idft(plan, spec, n_chan, rf, st);
-    stage_end(plan, 3, st);
-    return rc;
+    if (plan->path == SIMUS_PATH_PLAIN_F32) return plain_run(plan, tx, scat, nullptr, rf, st);
+    return tc_execute(plan, 1, &plan, tx, scat, nullptr, &rf, st);
 }
 
 int simus_pfield(simus_plan *plan, const simus_tx *tx, int64_t n_pts, const float *x,
                  const float *y, const float *z, int32_t n_freq, float *prms, void *stream) {
+    CaptureScope capture_scope(stream);
     if (!plan) return fail(SIMUS_ERR_ARG, "plan must not be NULL");
     for (bool &u : plan->stage_used) u = false;
     int rc;
@@ -583,6 +726,7 @@ int simus_pfield(simus_plan *plan, const simus_tx *tx, int64_t n_pts, const floa
 
 int simus_rf_grad(simus_plan *plan, const simus_tx *tx, const simus_scat *scat, const float *drf,
                   float *g_rc, float *g_x, float *g_z, float *g_delays, void *stream) {
+    CaptureScope capture_scope(stream);
     if (!plan) return fail(SIMUS_ERR_ARG, "plan must not be NULL");
     for (bool &u : plan->stage_used) u = false;
     int rc;
@@ -632,13 +776,34 @@ int simus_rf_grad(simus_plan *plan, const simus_tx *tx, const simus_scat *scat, 
 
 int simus_batch_rf(int32_t n_sims, simus_plan *const *plans, const simus_tx *tx,
                    const simus_scat *scat, float *const *rf, void *stream) {
+    CaptureScope capture_scope(stream);
     if (n_sims < 0 || (n_sims > 0 && (!plans || !tx || !scat || !rf)))
         return fail(SIMUS_ERR_ARG, "invalid batch arguments");
+    if (n_sims == 0) return SIMUS_OK;
+    int rc;
     for (int i = 0; i < n_sims; ++i) {
-        int rc = simus_rf(plans[i], &tx[i], &scat[i], rf[i], stream);
-        if (rc) return rc;
+        if (!plans[i]) return fail(SIMUS_ERR_ARG, "plans[%d] is NULL", i);
+        if (plans[i]->path != plans[0]->path || plans[i]->device != plans[0]->device)
+            return fail(SIMUS_ERR_ARG, "all plans of a batch must share path and device (plan %d)", i);
+        for (bool &u : plans[i]->stage_used) u = false;
     }
-    return SIMUS_OK;
+    if ((rc = use_plan_device(plans[0]))) return rc;
+    for (int i = 0; i < n_sims; ++i) {
+        if ((rc = validate_tx(plans[i], &tx[i])) || (rc = validate_scat(&scat[i])) ||
+            (rc = check_device_ptr(rf[i], "rf[i]")))
+            return fail(rc, "simulation %d: %s", i, simus_last_error());
+    }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (plans[0]->path == SIMUS_PATH_PLAIN_F32) {
+        for (int i = 0; i < n_sims; ++i) {
+            const size_t bytes = sizeof(float) * (size_t)tx[i].n_tx * plans[i]->N * plans[i]->nt;
+            rc = scat[i].n == 0 ? check_cuda(cudaMemsetAsync(rf[i], 0, bytes, st), "memset rf")
+                                : plain_run(plans[i], &tx[i], &scat[i], nullptr, rf[i], st);
+            if (rc) return rc;
+        }
+        return SIMUS_OK;
+    }
+    return tc_execute(plans[0], n_sims, plans, tx, scat, nullptr, rf, st);
 }
 
 }  // extern "C"

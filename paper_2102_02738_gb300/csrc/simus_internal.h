@@ -27,11 +27,8 @@ struct GreenConst {
     float inv_rf;     // 1 / R_f (0 without lens)
     float att2;       // (alpha_dB / 8.69) * df * 1e-4 * log2(e): base-2 absorption per bin per metre
     float zeta;       // Eq. 39
-    float ga[4];      // Re(B_g) / h^2
-    float gb[4];      // Im(B_g) / h^2
-    float ga2[4];     // (Re(B_g) / h^2)^2
-    float Cr[4];      // Re(A_g) sqrt(pi / 2)
-    float Ci[4];      // Im(A_g) sqrt(pi / 2)
+    float h;          // element height (delta is evaluated as h * f(h^2 alpha))
+    float h2;         // h^2
     int32_t narrow;   // 1 if |k b / nu| <= 3.2 at every kept bin (polynomial sinc suffices)
     int32_t pad2_;
     double df;        // fs / nt [Hz]
@@ -58,6 +55,11 @@ struct simus_plan {
     int *d_err = nullptr;             // device-side error flag (bounded waits)
     void *d_work = nullptr;           // workspace
     size_t work_bytes = 0;
+    void *h_stage = nullptr;          // pinned host staging of work descriptors
+    size_t h_stage_bytes = 0;
+    cudaEvent_t ev_stage = nullptr;   // recorded after the staging copy; guards reuse
+    bool stage_pending = false;
+    int items_per_sm = 4;             // tensor-core path: work items per SM (tuning)
     bool profiling = false;
     bool stage_used[SIMUS_N_STAGES] = {};
     cudaEvent_t ev[2 * SIMUS_N_STAGES] = {};
@@ -104,15 +106,47 @@ int launch_plain(const simus_plan *p, const PlainGeom &g, const simus_scat *sc, 
                  const float2 *cw, float2 *part, cudaStream_t st);
 
 // Batched tensor-core path (FP16 / BF16 operands, FP32 accumulation).
-struct TcGeom {
-    bool ok;             // the problem fits this kernel (N <= 128, 2T <= 256, smem)
-    int Np, nN, QB;      // padded elements, padded GEMM N (2T), bins per work item
-    int n_btiles, n_chunks, tiles_per_chunk, n_items, grid;
-    size_t smem, b1_bytes;
+// A simulation is cut into transmit groups of TG transmits (one "unit" each); every unit
+// is cut into work items of QB bins x tiles_per_chunk scatterer tiles.  The shapes are
+// chosen per simulation so that one CTA's operands fit shared memory and its
+// accumulators fit the 512 tensor-memory columns.
+struct TcShape {
+    bool ok;
+    int Np;              // elements padded to 8 (<= 256)
+    int TG, n_groups;    // transmits per group, groups
+    int nN;              // GEMM N of a group: 2 TG padded to 16
+    int mh;              // receive GEMM M-halves: 1 (Np <= 128) or 2
+    int pair;            // 1: bins generated in pairs into two tile buffers
+    int QB;              // bins per work item
+    int n_btiles;
+    int64_t n_tiles;     // scatterer tiles of 128
+    int tiles_per_chunk, n_chunks;
+    size_t smem;         // dynamic shared memory of the kernel for this shape
+    size_t b1_bytes;     // B1 operand images of one group: nq * nN * 2Np * 2
 };
-TcGeom tc_geometry(const simus_plan *p, int T, int64_t S);
-int launch_tc(const simus_plan *p, const TcGeom &g, const simus_tx *tx, const simus_scat *sc,
-              uint16_t *b1img, float2 *part, int *err, cudaStream_t st);
+// items_per_sm: target number of work items per SM over the whole launch (tuning).
+TcShape tc_shape(const simus_plan *p, int T, int64_t S, double work_share, int items_per_sm);
+
+// One (simulation, transmit group), as the kernel reads it.
+struct TcUnit {
+    GreenConst gc;
+    const SubElem *sub;
+    const float *x, *y, *z, *rc;
+    const float *delays, *apod;   // of the whole simulation, [T][N]
+    int64_t S, n_tiles;
+    int T, t0, TG;                // simulation transmits, group offset and size
+    int Np, nN, QB, mh, pair;
+    int n_btiles, n_chunks, tiles_per_chunk;
+    int pad_;
+    int64_t item0;                // first global item of this unit
+    uint16_t *b1img;              // [nq][nN * 2Np]
+    float2 *part;                 // [n_chunks][T][N][nq] of the simulation
+};
+// Launch the B1 image kernels of every unit and the persistent tensor-core kernel over
+// all items.  d_units: device copy of units (n_units), counter: zeroed device int.
+int launch_tc_units(const TcUnit *h_units, const TcUnit *d_units, int n_units, int64_t n_items,
+                    size_t smem, bool bf16, bool has_y, bool narrow, bool linear, int num_sms,
+                    int *counter, int *err, cudaStream_t st);
 
 // Adjoint (gradient) path, FP32.
 struct GradGeom {
