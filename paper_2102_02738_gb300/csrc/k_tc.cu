@@ -165,7 +165,7 @@ k_tc_rf(const TcUnit *__restrict__ units, int n_units, int64_t n_items, int *cou
                 reinterpret_cast<int *>(&U)[i] = reinterpret_cast<const int *>(&units[ui])[i];
             __syncthreads();
         }
-        const GreenConst &gc = U.gc;
+        const GreenConst gc = U.gc;   // register copy: the per-pair setup reads it often
         const int N = gc.N, nu = gc.nu, M = gc.M, nq = gc.nq;
         const int Np = U.Np, nN = U.nN, TG = U.TG, QB = U.QB, mh = U.mh, pair = U.pair;
         const int K1 = 2 * Np;
@@ -416,10 +416,26 @@ TcShape tc_shape(const simus_plan *p, int T, int64_t S, double work_share, int i
     g.n_groups = (T + g.TG - 1) / g.TG;
     g.n_btiles = (p->nq + g.QB - 1) / g.QB;
     g.n_tiles = std::max<int64_t>(1, (S + kSB - 1) / kSB);
-    // chunks: this simulation's share of ~items_per_sm items per SM
-    const double want = std::max(1.0, work_share * items_per_sm * p->num_sms);
-    int64_t chunks = (int64_t)std::ceil(want / ((double)g.n_btiles * g.n_groups));
-    chunks = std::max<int64_t>(1, std::min<int64_t>(chunks, std::max<int64_t>(1, g.n_tiles / 2)));
+    int64_t chunks;
+    if (work_share >= 0.999) {
+        // one simulation: the chunk count minimising the modelled makespan
+        // ceil(items / SMs) * tiles per item, items = bin tiles * groups * chunks
+        const int64_t per = (int64_t)g.n_btiles * g.n_groups;
+        double best = 1e300;
+        chunks = 1;
+        for (int64_t c = 1; c <= std::min<int64_t>(g.n_tiles, 64); ++c) {
+            const int64_t waves = (per * c + p->num_sms - 1) / p->num_sms;
+            const int64_t tiles = (g.n_tiles + c - 1) / c;
+            const double span = (double)waves * tiles * (1.0 + 0.002 * c);   // small cost per chunk
+            if (span < best) { best = span; chunks = c; }
+        }
+    } else {
+        // part of a batch: this simulation's share of ~items_per_sm items per SM; the
+        // dynamic work counter balances the rest
+        const double want = std::max(1.0, work_share * items_per_sm * p->num_sms);
+        chunks = (int64_t)std::ceil(want / ((double)g.n_btiles * g.n_groups));
+        chunks = std::max<int64_t>(1, std::min<int64_t>(chunks, std::max<int64_t>(1, g.n_tiles / 2)));
+    }
     g.tiles_per_chunk = (int)((g.n_tiles + chunks - 1) / chunks);
     g.n_chunks = (int)((g.n_tiles + g.tiles_per_chunk - 1) / g.tiles_per_chunk);
     g.b1_bytes = (size_t)p->nq * g.nN * 2 * g.Np * 2;
