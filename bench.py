@@ -36,6 +36,7 @@ WORKLOADS = {
     "diverging-convex-128": ph.diverging_convex_128,
     "focused-linear-64": ph.focused_linear_64,
     "planewave-linear-128-grad": ph.planewave_linear_128_grad,
+    "ragged-batch": ph.ragged_batch,
 }
 DEFAULT_WORKLOAD = "diverging-convex-128"
 DEFAULT_PATH = {"planewave-linear-128": "plain", "focused-linear-64": "plain",
@@ -363,6 +364,137 @@ def run_ours(args, rank, ws, local):
     plan.close()
 
 
+def run_batch_bench(args, rank, ws, local):
+    """Ragged batch: every simulation in one persistent tensor-core launch per step; the
+    whole simus_batch_rf call is captured once in a CUDA graph and replayed."""
+    import torch
+    from paper_2102_02738_gb300 import build as libbuild
+    libbuild.build()
+    from paper_2102_02738_gb300 import simus
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sims = ph.ragged_batch(n_sims=args.n_sims, scale=args.scale)
+    path = args.path or "tc_f16"
+    plans = [simus.Plan(w.cfg, path=path) for w in sims]
+    txs = [(torch.from_numpy(w.delays).to(dev), torch.from_numpy(w.apod).to(dev)) for w in sims]
+    scs = [(torch.from_numpy(w.x).to(dev), None, torch.from_numpy(w.z).to(dev),
+            torch.from_numpy(w.rc).to(dev)) for w in sims]
+    rfs = [torch.empty((w.n_tx, w.cfg["n_elements"], p.info["n_samples"]), device=dev)
+           for w, p in zip(sims, plans)]
+    terms = sum(float(p.info["n_bins"]) * w.n_scat * p.info["n_sub"] * w.cfg["n_elements"] * w.n_tx
+                for w, p in zip(sims, plans))
+    unique = sum(float(p.info["n_bins"]) * w.n_scat * p.info["n_sub"] * w.cfg["n_elements"]
+                 for w, p in zip(sims, plans))
+    st = torch.cuda.Stream(device=dev)
+    handles = [p.handle for p in plans]
+    with torch.cuda.stream(st):
+        simus.simus_batch_rf(handles, txs, scs, rfs, st)            # sizes workspaces
+    st.synchronize()
+    l0 = simus.simus_kernel_launches()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=st):
+        simus.simus_batch_rf(handles, txs, scs, rfs, st)
+    per_replay = simus.simus_kernel_launches() - l0
+    for _ in range(max(args.warmup, 0)):
+        g.replay()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.5)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    barrier(ws)
+    torch.cuda.synchronize()
+    cur = torch.cuda.current_stream()
+    for i in range(args.steps):
+        ev[i][0].record(cur)
+        g.replay()
+        ev[i][1].record(cur)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clk = clocks.stop()
+    ms = allreduce_max(sum(a.elapsed_time(b) for a, b in ev), ws) / args.steps
+    peaks, peak_src = measured_peaks()
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = alu_peak_terms(n_sm, float(peaks.get("sm_max_mhz", 2070.0)))
+    line = {"metric": METRIC, "value": terms * ws / (ms / 1e3), "unit": "terms/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f16" if path == "tc_f16" else path, "data": "synthetic",
+            "config": {"workload": "ragged-batch", "sims": len(sims), "scale": args.scale,
+                       "scatterers_total": int(sum(w.n_scat for w in sims)),
+                       "elements": [min(w.cfg["n_elements"] for w in sims), max(w.cfg["n_elements"] for w in sims)],
+                       "transmits": [min(w.n_tx for w in sims), max(w.n_tx for w in sims)],
+                       "terms_per_step": terms, "unique_terms_per_step": unique,
+                       "execution": "one persistent launch per step, captured CUDA graph",
+                       "l2": "inputs and outputs exceed L2"},
+            "roofline": {"bound": "alu", "achieved": unique / (ms / 1e3) / 1e9, "peak": peak / 1e9,
+                         "unit": "Gterm/s", "frac": unique / (ms / 1e3) / peak,
+                         "note": "whole step (weights + persistent kernel + reductions + iDFTs)",
+                         "peak_source": peak_src},
+            "gpu_launches": per_replay * args.steps, "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    for p in plans:
+        p.close()
+
+
+def run_grad_bench(args, rank, ws, local):
+    """Forward RF plus the adjoint (simus_rf_grad) of the RF misfit, FP32."""
+    import torch
+    from paper_2102_02738_gb300 import build as libbuild
+    libbuild.build()
+    from paper_2102_02738_gb300 import simus
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = ph.planewave_linear_128_grad(**({"n_scat": args.n_scat} if args.n_scat else {}))
+    path = args.path or "plain"
+    plan = simus.Plan(w.cfg, path=path)
+    d = {k: torch.from_numpy(np.ascontiguousarray(getattr(w, k))).to(dev)
+         for k in ("delays", "apod", "x", "z", "rc")}
+    tgt = plan.rf(d["delays"], d["apod"], torch.from_numpy(w.extra["x_target"]).to(dev), None,
+                  torch.from_numpy(w.extra["z_target"]).to(dev), d["rc"])
+    info = plan.info
+    terms = float(info["n_bins"]) * w.n_scat * info["n_sub"] * w.cfg["n_elements"] * w.n_tx
+
+    def step():
+        rf = plan.rf(d["delays"], d["apod"], d["x"], None, d["z"], d["rc"])
+        drf = 2.0 * (rf - tgt)
+        return plan.rf_grad(d["delays"], d["apod"], d["x"], None, d["z"], d["rc"], drf)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    simus.simus_plan_set_profiling(plan.handle, True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    cur = torch.cuda.current_stream()
+    fwd, bwd = [], []
+    for i in range(args.steps):
+        ev[i][0].record(cur)
+        rf = plan.rf(d["delays"], d["apod"], d["x"], None, d["z"], d["rc"])
+        fwd.append(simus.simus_plan_get_timings(plan.handle))
+        drf = 2.0 * (rf - tgt)
+        plan.rf_grad(d["delays"], d["apod"], d["x"], None, d["z"], d["rc"], drf)
+        bwd.append(simus.simus_plan_get_timings(plan.handle))
+        ev[i][1].record(cur)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    fwd_ms = statistics.mean(sum(t.values()) for t in fwd)
+    bwd_ms = statistics.mean(sum(t.values()) for t in bwd)
+    line = {"metric": METRIC + ", forward + adjoint", "value": terms / (ms / 1e3), "unit": "terms/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "planewave-linear-128-grad", "forward_path": path,
+                       "scatterers": w.n_scat, "transmits": w.n_tx, "bins": info["n_bins"],
+                       "terms_per_step": terms},
+            "forward_ms": fwd_ms, "adjoint_ms": bwd_ms,
+            "adjoint_stages_ms": {k: statistics.mean(t[k] for t in bwd) for k in simus.STAGES}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -376,10 +508,16 @@ def main():
     ap.add_argument("--no-plain-compare", action="store_true")
     ap.add_argument("--n-scat", type=int, default=0,
                     help="override the workload's scatterer count (profiling of small cases)")
+    ap.add_argument("--n-sims", type=int, default=256, help="ragged-batch: simulations")
+    ap.add_argument("--scale", type=float, default=1.0, help="ragged-batch: scatterer count scale")
     args = ap.parse_args()
     rank, ws, local = dist_init()
     if args.impl == "reference":
         run_reference(args, rank, ws)
+    elif args.workload == "ragged-batch":
+        run_batch_bench(args, rank, ws, local)
+    elif args.workload == "planewave-linear-128-grad":
+        run_grad_bench(args, rank, ws, local)
     else:
         run_ours(args, rank, ws, local)
     if ws > 1:

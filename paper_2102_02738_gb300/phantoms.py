@@ -144,11 +144,16 @@ def rf_length(cfg, x, z, delays, y=None) -> int:
     half = cfg["width"] / 2.0
     y2 = 0.0 if y is None else float(np.max(np.asarray(y, np.float64) ** 2))
     xs, zs = np.asarray(x, np.float64), np.asarray(z, np.float64)
+    if cfg["radius"] <= 0:
+        # linear array: (x - x_e)^2 is convex in x_e, so the farthest edge is an end one
+        xe, ze = np.array([xe.min(), xe.max()]), np.zeros(2)
     r2 = 0.0
-    for sgn in (-1.0, 1.0):
-        dx = xs[:, None] - (xe[None, :] + sgn * half)
-        dz = zs[:, None] - ze[None, :]
-        r2 = max(r2, float(np.max(dx * dx + dz * dz)))
+    for s0 in range(0, len(xs), 1 << 16):
+        xc, zc = xs[s0:s0 + (1 << 16)], zs[s0:s0 + (1 << 16)]
+        for sgn in (-1.0, 1.0):
+            dx = xc[:, None] - (xe[None, :] + sgn * half)
+            dz = zc[:, None] - ze[None, :]
+            r2 = max(r2, float(np.max(dx * dx + dz * dz)))
     r_max = math.sqrt(r2 + y2)
     t = 2.0 * r_max / cfg["c"] + float(np.max(delays)) + 8.0 / cfg["fc"]
     n = int(math.ceil(cfg["fs"] * t))
