@@ -58,25 +58,27 @@ size_t unit_smem(int Np, int nN, int pair, int M) {
 }
 }  // namespace
 
-// B1 images of one unit: per kept bin, the nN x 2Np K-major operand of the transmit GEMM
-// for transmits t0 .. t0 + TG - 1,
+// B1 images of one simulation: per kept bin and transmit group g, the nN x 2Np K-major
+// operand of the transmit GEMM for transmits g TG .. g TG + TG - 1 (image [k][g]),
 //   row 2t: (Re C, -Im C), row 2t+1: (Im C, Re C), C = W exp(i 2 pi frac(q df dtau)).
 template <bool BF16>
-__global__ void k_tc_weights(int TG, int N, int Np, int nN, int nq, int q_lo, double df,
-                             const float *__restrict__ delays, const float *__restrict__ apod,
-                             uint16_t *__restrict__ img) {
+__global__ void k_tc_weights(int T, int G, int TG, int N, int Np, int nN, int nq, int q_lo,
+                             double df, const float *__restrict__ delays,
+                             const float *__restrict__ apod, uint16_t *__restrict__ img) {
     const int K = 2 * Np;
-    const int64_t per_bin = (int64_t)nN * K;
-    const int64_t total = per_bin * nq;
+    const int64_t per_img = (int64_t)nN * K;
+    const int64_t total = per_img * G * nq;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x) {
-        int k = (int)(i / per_bin);
-        int r = (int)(i % per_bin);
+        const int64_t kg = i / per_img;
+        int k = (int)(kg / G), g = (int)(kg % G);
+        int r = (int)(i % per_img);
         int n = r / K, kk = r % K;
-        int t = n >> 1;
+        int tl = n >> 1;
+        int t = g * TG + tl;
         int e = kk < Np ? kk : kk - Np;
         float v = 0.f;
-        if (t < TG && e < N) {
+        if (tl < TG && t < T && e < N) {
             double ph = (double)(q_lo + k) * ((double)delays[t * N + e] * df);
             ph -= rint(ph);
             float s, c;
@@ -86,7 +88,7 @@ __global__ void k_tc_weights(int TG, int N, int Np, int nN, int nq, int q_lo, do
             bool first_half = kk < Np;
             v = (n & 1) ? (first_half ? ci : cr) : (first_half ? cr : -ci);
         }
-        img[(size_t)k * per_bin + tc::kmajor_offset(n, kk, K) / 2] = h16<BF16>(v);
+        img[(size_t)kg * per_img + tc::kmajor_offset(n, kk, K) / 2] = h16<BF16>(v);
     }
 }
 
@@ -168,6 +170,7 @@ k_tc_rf(const TcUnit *__restrict__ units, int n_units, int64_t n_items, int *cou
         const GreenConst gc = U.gc;   // register copy: the per-pair setup reads it often
         const int N = gc.N, nu = gc.nu, M = gc.M, nq = gc.nq;
         const int Np = U.Np, nN = U.nN, TG = U.TG, QB = U.QB, mh = U.mh, pair = U.pair;
+        const int G = U.G, T = U.T;
         const int K1 = 2 * Np;
         const size_t abytes = (size_t)kSB * K1 * 2;
         unsigned char *A0 = dyn;
@@ -186,10 +189,10 @@ k_tc_rf(const TcUnit *__restrict__ units, int n_units, int64_t n_items, int *cou
             cur_unit = ui;
             __syncthreads();
         }
-        auto issue_b1 = [&](int k) {
+        auto issue_b1 = [&](int k, int g) {   // weights of bin k, transmit group g
             if (tid == 0) {
                 tc::mbar_arrive_expect_tx(mbar_b1, b1_bytes);
-                tc::bulk_g2s(b1s, U.b1img + (size_t)k * nN * K1, b1_bytes, mbar_b1);
+                tc::bulk_g2s(b1s, U.b1img + ((size_t)k * G + g) * nN * K1, b1_bytes, mbar_b1);
                 b1_inflight = true;
             }
         };
@@ -205,7 +208,7 @@ k_tc_rf(const TcUnit *__restrict__ units, int n_units, int64_t n_items, int *cou
                 const int nb = min(step, QB - bp);
                 const int kA = min(k0 + bp, nq - 1);       // bins past the end repeat the last
                 const int kB = min(k0 + bp + 1, nq - 1);   // (their outputs are discarded)
-                issue_b1(kA);
+                issue_b1(kA, 0);
                 if (pending2) {   // tile buffers and B2 still read by the last MMA2
                     if (!wait_all(mbar2, ph2)) { aborted = true; break; }
                     ph2 ^= 1;
@@ -266,7 +269,10 @@ k_tc_rf(const TcUnit *__restrict__ units, int n_units, int64_t n_items, int *cou
                 __syncthreads();
                 tc::fence_after_sync();
 
-                for (int bi_ = 0; bi_ < nb && !aborted; ++bi_) {
+                // every bin of the pair, every transmit group: MMA1 -> P' -> MMA2
+                for (int si = 0; si < nb * G && !aborted; ++si) {
+                    const int bi_ = si / G, g = si - bi_ * G;
+                    const int TGg = min(TG, T - g * TG);      // transmits of this group
                     const uint32_t abase = bi_ ? abuf1 : abuf0;
                     // ---- MMA1: D1 = A * B1^T
                     if (tid == 0) {
@@ -287,7 +293,10 @@ k_tc_rf(const TcUnit *__restrict__ units, int n_units, int64_t n_items, int *cou
                     if (!wait_all(mbar1, ph1)) { aborted = true; break; }
                     ph1 ^= 1;
                     tc::fence_after_sync();
-                    if (bi_ + 1 < nb) issue_b1(kB);           // B1 is free again
+                    if (si + 1 < nb * G) {                     // B1 is free again
+                        const int sn = si + 1;
+                        issue_b1(sn / G ? kB : kA, sn % G);
+                    }
                     if (pending2) {                            // B2 still read by MMA2
                         if (!wait_all(mbar2, ph2)) { aborted = true; break; }
                         ph2 ^= 1;
@@ -305,7 +314,7 @@ k_tc_rf(const TcUnit *__restrict__ units, int n_units, int64_t n_items, int *cou
                             for (int i = 0; i < 8; ++i) {
                                 const int t = (c0 >> 1) + i;
                                 float pr = 0.f, pi = 0.f;
-                                if (t < TG) { pr = R * v[2 * i]; pi = R * v[2 * i + 1]; }
+                                if (t < TGg) { pr = R * v[2 * i]; pi = R * v[2 * i + 1]; }
                                 const int n0 = 2 * t;
                                 *reinterpret_cast<uint16_t *>(B2 + tc::kmajor_offset(n0, s, 256)) = h16<BF16>(pr);
                                 *reinterpret_cast<uint16_t *>(B2 + tc::kmajor_offset(n0, 128 + s, 256)) = h16<BF16>(-pi);
@@ -326,7 +335,7 @@ k_tc_rf(const TcUnit *__restrict__ units, int n_units, int64_t n_items, int *cou
                     // between MN-adjacent core matrices (element groups, 128 bytes).
                     if (tid == 0) {
                         for (int h = 0; h < mh; ++h) {
-                            const uint32_t d2 = tmem + (uint32_t)(nN * (1 + (bp + bi_) * mh + h));
+                            const uint32_t d2 = tmem + (uint32_t)(nN * (1 + ((bp + bi_) * G + g) * mh + h));
                             for (int j = 0; j < 16; ++j) {
                                 const uint32_t a0 = abase + (uint32_t)((2 * (j & 7)) * 16 * K1)
                                                   + (uint32_t)((j >> 3) * (Np / 8) * 128) + (uint32_t)(h * 16 * 128);
@@ -348,23 +357,25 @@ k_tc_rf(const TcUnit *__restrict__ units, int n_units, int64_t n_items, int *cou
             pending2 = false;
         }
         tc::fence_after_sync();
-        // ---- partial spectra of this item: part[chunk][t0 + t][e][k]
+        // ---- partial spectra of this item: part[chunk][g TG + t][e][k]
         {
             const int sp = warp & 3, cc = warp >> 2;
-            for (int b = 0; b < QB; ++b) {
+            for (int bg = 0; bg < QB * G; ++bg) {
+                const int b = bg / G, g = bg - b * G;
                 const int k = k0 + b;
+                const int TGg = min(TG, T - g * TG);
                 for (int h = 0; h < mh; ++h) {
                     const int e = 128 * h + sp * 32 + lane;
                     for (int c0 = cc * 16; c0 < nN; c0 += 64) {
                         float v[16];
                         tc::tmem_ld16(tmem + ((uint32_t)(sp * 32) << 16) +
-                                          (uint32_t)(nN * (1 + b * mh + h) + c0), v);
+                                          (uint32_t)(nN * (1 + bg * mh + h) + c0), v);
                         if (k < nq && e < N) {
 #pragma unroll
                             for (int i = 0; i < 8; ++i) {
                                 const int t = (c0 >> 1) + i;
-                                if (t < TG)
-                                    U.part[(((size_t)chunk * U.T + U.t0 + t) * N + e) * nq + k] =
+                                if (t < TGg)
+                                    U.part[(((size_t)chunk * T + g * TG + t) * N + e) * nq + k] =
                                         make_float2(v[2 * i], v[2 * i + 1]);
                             }
                         }
@@ -394,33 +405,33 @@ TcShape tc_shape(const simus_plan *p, int T, int64_t S, double work_share, int i
     if (g.Np > 256) return g;
     g.mh = g.Np > 128 ? 2 : 1;
     const size_t limit = 227 * 1024 - kHeader - 1024;
-    for (int TG = std::min(T, 120); TG >= 1; TG = (TG > 8 ? TG - 8 : TG - 1)) {
-        const int nN = ((2 * TG + 15) / 16) * 16;
-        const int qb = (512 - nN) / (nN * g.mh);
-        if (qb < 1) continue;
-        for (int pair = 1; pair >= 0; --pair) {
-            if (pair && qb < 2) continue;
+    // Two tile buffers (geometry shared by bin pairs) with at most two transmit groups,
+    // else one buffer with the largest group that fits; tensor memory holds D1 and
+    // QB * G * mh accumulator slices of nN columns.
+    for (int pair = 1; pair >= 0 && !g.ok; --pair) {
+        for (int TG = std::min(T, 120); TG >= 1 && !g.ok; TG = (TG > 8 ? TG - 8 : TG - 1)) {
+            const int nN = ((2 * TG + 15) / 16) * 16;
+            const int G = (T + TG - 1) / TG;
+            if (pair && G > 2) break;
+            const int qb = (512 - nN) / (nN * G * g.mh);
+            if (qb < (pair ? 2 : 1)) continue;
             const size_t sm = unit_smem(g.Np, nN, pair, p->M);
-            if (sm <= limit) {
-                g.ok = true;
-                g.TG = TG; g.nN = nN; g.pair = pair;
-                g.QB = std::min(4, qb);
-                if (pair && (g.QB & 1)) g.QB -= 1;
-                g.smem = sm + kHeader;
-                break;
-            }
+            if (sm > limit) continue;
+            g.ok = true;
+            g.TG = TG; g.nN = nN; g.pair = pair; g.n_groups = G;
+            g.QB = std::min(4, qb);
+            if (pair && (g.QB & 1)) g.QB -= 1;
+            g.smem = sm + kHeader;
         }
-        if (g.ok) break;
     }
     if (!g.ok) return g;
-    g.n_groups = (T + g.TG - 1) / g.TG;
     g.n_btiles = (p->nq + g.QB - 1) / g.QB;
     g.n_tiles = std::max<int64_t>(1, (S + kSB - 1) / kSB);
     int64_t chunks;
     if (work_share >= 0.999) {
         // one simulation: the chunk count minimising the modelled makespan
-        // ceil(items / SMs) * tiles per item, items = bin tiles * groups * chunks
-        const int64_t per = (int64_t)g.n_btiles * g.n_groups;
+        // ceil(items / SMs) * tiles per item, items = bin tiles * chunks
+        const int64_t per = (int64_t)g.n_btiles;
         double best = 1e300;
         chunks = 1;
         for (int64_t c = 1; c <= std::min<int64_t>(g.n_tiles, 64); ++c) {
@@ -433,12 +444,12 @@ TcShape tc_shape(const simus_plan *p, int T, int64_t S, double work_share, int i
         // part of a batch: this simulation's share of ~items_per_sm items per SM; the
         // dynamic work counter balances the rest
         const double want = std::max(1.0, work_share * items_per_sm * p->num_sms);
-        chunks = (int64_t)std::ceil(want / ((double)g.n_btiles * g.n_groups));
+        chunks = (int64_t)std::ceil(want / (double)g.n_btiles);
         chunks = std::max<int64_t>(1, std::min<int64_t>(chunks, std::max<int64_t>(1, g.n_tiles / 2)));
     }
     g.tiles_per_chunk = (int)((g.n_tiles + chunks - 1) / chunks);
     g.n_chunks = (int)((g.n_tiles + g.tiles_per_chunk - 1) / g.tiles_per_chunk);
-    g.b1_bytes = (size_t)p->nq * g.nN * 2 * g.Np * 2;
+    g.b1_bytes = (size_t)p->nq * g.n_groups * g.nN * 2 * g.Np * 2;
     return g;
 }
 
@@ -453,15 +464,14 @@ int launch_tc_units(const TcUnit *h_units, const TcUnit *d_units, int n_units, i
                     int *counter, int *err, cudaStream_t st) {
     for (int u = 0; u < n_units; ++u) {
         const TcUnit &U = h_units[u];
-        int64_t total = (int64_t)U.gc.nq * U.nN * 2 * U.Np;
+        int64_t total = (int64_t)U.gc.nq * U.G * U.nN * 2 * U.Np;
         int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)num_sms * 16);
-        const float *dl = U.delays + (size_t)U.t0 * U.gc.N, *ap = U.apod + (size_t)U.t0 * U.gc.N;
         if (bf16)
-            k_tc_weights<true><<<blocks, 256, 0, st>>>(U.TG, U.gc.N, U.Np, U.nN, U.gc.nq, U.gc.q_lo,
-                                                       U.gc.df, dl, ap, U.b1img);
+            k_tc_weights<true><<<blocks, 256, 0, st>>>(U.T, U.G, U.TG, U.gc.N, U.Np, U.nN, U.gc.nq,
+                                                       U.gc.q_lo, U.gc.df, U.delays, U.apod, U.b1img);
         else
-            k_tc_weights<false><<<blocks, 256, 0, st>>>(U.TG, U.gc.N, U.Np, U.nN, U.gc.nq, U.gc.q_lo,
-                                                        U.gc.df, dl, ap, U.b1img);
+            k_tc_weights<false><<<blocks, 256, 0, st>>>(U.T, U.G, U.TG, U.gc.N, U.Np, U.nN, U.gc.nq,
+                                                        U.gc.q_lo, U.gc.df, U.delays, U.apod, U.b1img);
         count_launches(1);
         int rc = check_cuda(cudaGetLastError(), "k_tc_weights launch");
         if (rc) return rc;

@@ -506,7 +506,7 @@ int tc_execute(simus_plan *owner, int n, simus_plan *const *plans, const simus_t
             return fail(SIMUS_ERR_UNSUPPORTED, "tensor-core path: simulation %d (N=%d, nu=%d) does not fit",
                         i, p->N, p->nu);
         smem = std::max(smem, sh[j].smem);
-        n_units += sh[j].n_groups;
+        n_units += 1;
         has_y = has_y || scs[i].y != nullptr;
         narrow = narrow && p->gc.narrow;
         linear = linear && p->probe.radius <= 0;
@@ -518,7 +518,7 @@ int tc_execute(simus_plan *owner, int n, simus_plan *const *plans, const simus_t
     {
         int u = 0;
         for (int j = 0; j < nl; ++j)
-            for (int g = 0; g < sh[j].n_groups; ++g, ++u) { b1_off[u] = off; off += align256(sh[j].b1_bytes); }
+            { b1_off[u] = off; off += align256(sh[j].b1_bytes); ++u; }
         for (int j = 0; j < nl; ++j) {
             const simus_plan *p = plans[live[j]];
             part_off[j] = off;
@@ -568,22 +568,20 @@ int tc_execute(simus_plan *owner, int n, simus_plan *const *plans, const simus_t
             const int i = live[j];
             const simus_plan *p = plans[i];
             const TcShape &s = sh[j];
-            for (int g = 0; g < s.n_groups; ++g, ++u) {
-                TcUnit U{};
-                U.gc = p->gc;
-                U.sub = p->d_sub;
-                U.x = scs[i].x; U.y = scs[i].y; U.z = scs[i].z; U.rc = scs[i].rc;
-                U.delays = txs[i].delays; U.apod = txs[i].apod;
-                U.S = scs[i].n; U.n_tiles = s.n_tiles;
-                U.T = txs[i].n_tx; U.t0 = g * s.TG; U.TG = std::min(s.TG, U.T - U.t0);
-                U.Np = s.Np; U.mh = s.mh; U.pair = s.pair; U.QB = s.QB;
-                U.nN = ((2 * U.TG + 15) / 16) * 16;
-                U.n_btiles = s.n_btiles; U.n_chunks = s.n_chunks; U.tiles_per_chunk = s.tiles_per_chunk;
-                U.b1img = reinterpret_cast<uint16_t *>(base + b1_off[u]);
-                U.part = reinterpret_cast<float2 *>(base + part_off[j]);
-                hu[u] = U;
-                order.push_back({(double)s.QB * s.tiles_per_chunk * s.Np * p->nu, u});
-            }
+            TcUnit U{};
+            U.gc = p->gc;
+            U.sub = p->d_sub;
+            U.x = scs[i].x; U.y = scs[i].y; U.z = scs[i].z; U.rc = scs[i].rc;
+            U.delays = txs[i].delays; U.apod = txs[i].apod;
+            U.S = scs[i].n; U.n_tiles = s.n_tiles;
+            U.T = txs[i].n_tx; U.G = s.n_groups; U.TG = s.TG;
+            U.Np = s.Np; U.mh = s.mh; U.pair = s.pair; U.QB = s.QB; U.nN = s.nN;
+            U.n_btiles = s.n_btiles; U.n_chunks = s.n_chunks; U.tiles_per_chunk = s.tiles_per_chunk;
+            U.b1img = reinterpret_cast<uint16_t *>(base + b1_off[u]);
+            U.part = reinterpret_cast<float2 *>(base + part_off[j]);
+            hu[u] = U;
+            order.push_back({(double)s.QB * s.tiles_per_chunk * s.Np * p->nu, u});
+            ++u;
         }
     }
     // heaviest items first; item0 = prefix of item counts in that order

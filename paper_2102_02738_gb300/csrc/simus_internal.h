@@ -106,10 +106,11 @@ int launch_plain(const simus_plan *p, const PlainGeom &g, const simus_scat *sc, 
                  const float2 *cw, float2 *part, cudaStream_t st);
 
 // Batched tensor-core path (FP16 / BF16 operands, FP32 accumulation).
-// A simulation is cut into transmit groups of TG transmits (one "unit" each); every unit
-// is cut into work items of QB bins x tiles_per_chunk scatterer tiles.  The shapes are
+// A simulation ("unit") is cut into work items of QB bins x tiles_per_chunk scatterer
+// tiles; its transmits are contracted in G groups of TG inside every item, so that the
+// Green's tile is generated once whatever the number of transmits.  The shapes are
 // chosen per simulation so that one CTA's operands fit shared memory and its
-// accumulators fit the 512 tensor-memory columns.
+// accumulators (D1 + QB G mh slices of nN columns) fit the 512 tensor-memory columns.
 struct TcShape {
     bool ok;
     int Np;              // elements padded to 8 (<= 256)
@@ -127,19 +128,19 @@ struct TcShape {
 // items_per_sm: target number of work items per SM over the whole launch (tuning).
 TcShape tc_shape(const simus_plan *p, int T, int64_t S, double work_share, int items_per_sm);
 
-// One (simulation, transmit group), as the kernel reads it.
+// One simulation, as the kernel reads it.
 struct TcUnit {
     GreenConst gc;
     const SubElem *sub;
     const float *x, *y, *z, *rc;
     const float *delays, *apod;   // of the whole simulation, [T][N]
     int64_t S, n_tiles;
-    int T, t0, TG;                // simulation transmits, group offset and size
+    int T, G, TG;                 // simulation transmits, transmit groups, group size
     int Np, nN, QB, mh, pair;
     int n_btiles, n_chunks, tiles_per_chunk;
     int pad_;
     int64_t item0;                // first global item of this unit
-    uint16_t *b1img;              // [nq][nN * 2Np]
+    uint16_t *b1img;              // [nq][G][nN * 2Np]
     float2 *part;                 // [n_chunks][T][N][nq] of the simulation
 };
 // Launch the B1 image kernels of every unit and the persistent tensor-core kernel over
