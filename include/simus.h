@@ -205,6 +205,33 @@ int simus_plan_check(simus_plan *plan);
 int simus_plan_set_profiling(simus_plan *plan, int32_t enable);
 int simus_plan_get_timings(simus_plan *plan, float *ms);
 
+/* Launch shapes of the tensor-core path (tuning; results do not depend on them beyond
+ * FP32 summation order, except delta_table, which trades the direct Eq. 16-18 evaluation
+ * for a cubic Hermite table of relative error <= 2.3e-6).  A field < 0 (chunks: <= 0)
+ * selects the library's default; simus_plan_get_tuning reports the values in force.
+ *   items_per_sm  batches: work items per SM the scatterer chunking aims at (default 4)
+ *   max_bins      frequency bins per work item, upper bound (default 4; tensor memory
+ *                 may allow fewer)
+ *   pair          1: bins generated two at a time into two tile buffers where shared
+ *                 memory allows (default), 0: one buffer
+ *   delta_table   1: delta from the table where Y = 0 (default), 0: direct evaluation
+ *   chunks        single simulations: scatterer chunks per bin tile (default: chosen by a
+ *                 makespan model over the SMs)
+ * The project's autotuner (paper_2102_02738_gb300/autotune.py) times candidates through
+ * these calls and caches the fastest per problem shape.
+ * Returns SIMUS_ERR_ARG for a NULL plan or values out of range (max_bins > 64,
+ * items_per_sm > 1024, chunks > 65536). */
+typedef struct simus_tuning {
+    int32_t items_per_sm;
+    int32_t max_bins;
+    int32_t pair;
+    int32_t delta_table;
+    int32_t chunks;
+    int32_t reserved[3];
+} simus_tuning;
+int simus_plan_set_tuning(simus_plan *plan, const simus_tuning *tuning);
+int simus_plan_get_tuning(const simus_plan *plan, simus_tuning *tuning);
+
 /* Number of kernels this library has launched in the process so far (tracing). */
 int64_t simus_kernel_launches(void);
 

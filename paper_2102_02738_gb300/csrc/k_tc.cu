@@ -50,11 +50,127 @@ __device__ __forceinline__ uint32_t h16x2(float lo, float hi) {
     return (uint32_t)h16<BF16>(lo) | ((uint32_t)h16<BF16>(hi) << 16);
 }
 
+// delta / h from the cubic Hermite table at x (clamped into the table; `in` tells
+// whether x was inside, else the caller evaluates it directly).
+__device__ __forceinline__ float2 tab_delta(const float4 *__restrict__ tab, float x, float x0,
+                                            float inv_dx, int n, bool &in) {
+    float t = (x - x0) * inv_dx;
+    in = t >= 0.0f && t < (float)(n - 1);
+    t = fminf(fmaxf(t, 0.0f), (float)(n - 1) - 0.5f);
+    const float fl = floorf(t);
+    const int i = (int)fl;
+    const float u = t - fl, u2 = u * u, u3 = u2 * u;
+    const float h01 = fmaf(-2.0f, u3, 3.0f * u2), h00 = 1.0f - h01;
+    const float h11 = u3 - u2, h10 = h11 - u2 + u;
+    const float4 a = tab[i], b = tab[i + 1];
+    return make_float2(fmaf(h00, a.x, fmaf(h10, a.z, fmaf(h01, b.x, h11 * b.z))),
+                       fmaf(h00, a.y, fmaf(h10, a.w, fmaf(h01, b.y, h11 * b.w))));
+}
+
+// Sub-element sums (Eq. 33) of the Green's terms of elements e0 and e0 + 1 for one
+// scatterer at bins qA (and qB = qA + 1 when NB = 2): two independent evaluation chains
+// side by side, so that each warp has twice the instruction-level parallelism.  An
+// element past N is evaluated on element N - 1 with zero amplitude (no branch).
+// o[c][b] = (Re, Im) of element e0 + c at bin b.
+template <int NB, bool TAB, bool HAS_Y, bool NARROW, bool LINEAR>
+__device__ __forceinline__ void gen_two(const GreenConst &gc, const SubElem *sub,
+                                        const float4 *tabs, const float4 &ps, int e0, float qA,
+                                        float qB, float (&o)[2][NB][2]) {
+    const int N = gc.N, nu = gc.nu;
+    const float w0 = e0 < N ? 1.0f : 0.0f, w1 = e0 + 1 < N ? 1.0f : 0.0f;
+    const int b0 = min(e0, N - 1) * nu, b1 = min(e0 + 1, N - 1) * nu;
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int b = 0; b < NB; ++b) o[c][b][0] = o[c][b][1] = 0.0f;
+    for (int mu = 0; mu < nu; ++mu) {
+        PairSetup P[2];
+        P[0] = pair_setup_f32<HAS_Y, LINEAR>(gc, sub[b0 + mu], ps.x, ps.y, ps.z, qA);
+        P[1] = pair_setup_f32<HAS_Y, LINEAR>(gc, sub[b1 + mu], ps.x, ps.y, ps.z, qA);
+        P[0].amp0 *= w0;
+        P[1].amp0 *= w1;
+        float er[2][NB], ei[2][NB];
+        float2 d[2][NB];
+        bool in_all = true;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const float q = b ? qB : qA;
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const float fr = df_frac_mul(q, P[c].u);
+                float sn, cs;
+                sincos_a(6.283185307179586f * fr, sn, cs);
+                const float amp = b ? P[c].amp0 * P[c].mstep : P[c].amp0;
+                const float m = amp * sinc_f<NARROW>(q * P[c].xb);
+                er[c][b] = cs * m;
+                ei[c][b] = sn * m;
+                if (TAB) {
+                    bool in;
+                    d[c][b] = tab_delta(tabs, q * P[c].kap, gc.tab_x0, gc.tab_inv_dx, gc.tab_n, in);
+                    in_all = in_all && in;
+                } else {
+                    d[c][b] = delta_f<HAS_Y>(gc, P[c], q);
+                }
+            }
+        }
+        if (TAB && !in_all) {   // rare: x outside the table (a scatterer within 2 mm)
+#pragma unroll
+            for (int b = 0; b < NB; ++b)
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const float q = b ? qB : qA;
+                    const float t = (q * P[c].kap - gc.tab_x0) * gc.tab_inv_dx;
+                    if (!(t >= 0.0f && t < (float)(gc.tab_n - 1))) d[c][b] = delta_f<false>(gc, P[c], q);
+                }
+        }
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                o[c][b][0] += er[c][b] * d[c][b].x - ei[c][b] * d[c][b].y;
+                o[c][b][1] += er[c][b] * d[c][b].y + ei[c][b] * d[c][b].x;
+            }
+    }
+}
+
+// One generation pass over a scatterer tile: every (scatterer, group of 8 elements)
+// item, written as FP16/BF16 rows of the K-major tile(s) A0 (bin qA) and A1 (bin qB).
+template <int NB, bool TAB, bool HAS_Y, bool BF16, bool NARROW, bool LINEAR>
+__device__ __forceinline__ void gen_tiles(const GreenConst &gc, const SubElem *sub,
+                                          const float4 *tabs, const float4 *sc, int Np,
+                                          float qA, float qB, unsigned char *A0,
+                                          unsigned char *A1, int tid) {
+    const int K1 = 2 * Np;
+    const int n_groups = Np >> 3;
+    for (int it = tid; it < kSB * n_groups; it += kThreads) {
+        const int s = it & (kSB - 1), eg = it >> 7;
+        const float4 ps = sc[s];
+        uint32_t pr[4], pi[4], qr[4], qi[4];
+#pragma unroll
+        for (int jp = 0; jp < 4; ++jp) {
+            float o[2][NB][2];
+            gen_two<NB, TAB, HAS_Y, NARROW, LINEAR>(gc, sub, tabs, ps, eg * 8 + 2 * jp, qA, qB, o);
+            pr[jp] = h16x2<BF16>(o[0][0][0], o[1][0][0]);
+            pi[jp] = h16x2<BF16>(o[0][0][1], o[1][0][1]);
+            if (NB == 2) {
+                qr[jp] = h16x2<BF16>(o[0][NB - 1][0], o[1][NB - 1][0]);
+                qi[jp] = h16x2<BF16>(o[0][NB - 1][1], o[1][NB - 1][1]);
+            }
+        }
+        *reinterpret_cast<uint4 *>(A0 + tc::kmajor_offset(s, eg * 8, K1)) = make_uint4(pr[0], pr[1], pr[2], pr[3]);
+        *reinterpret_cast<uint4 *>(A0 + tc::kmajor_offset(s, Np + eg * 8, K1)) = make_uint4(pi[0], pi[1], pi[2], pi[3]);
+        if (NB == 2) {
+            *reinterpret_cast<uint4 *>(A1 + tc::kmajor_offset(s, eg * 8, K1)) = make_uint4(qr[0], qr[1], qr[2], qr[3]);
+            *reinterpret_cast<uint4 *>(A1 + tc::kmajor_offset(s, Np + eg * 8, K1)) = make_uint4(qi[0], qi[1], qi[2], qi[3]);
+        }
+    }
+}
+
 // shared memory a unit needs after the header
-size_t unit_smem(int Np, int nN, int pair, int M) {
+size_t unit_smem(int Np, int nN, int pair, int M, int tab_n) {
     const size_t a = (size_t)kSB * 2 * Np * 2;
     return (pair ? 2 : 1) * a + (size_t)nN * 2 * Np * 2 + (size_t)nN * 256 * 2
-         + sizeof(float4) * kSB + sizeof(SubElem) * M;
+         + sizeof(float4) * kSB + sizeof(SubElem) * M + sizeof(float4) * tab_n;
 }
 }  // namespace
 
@@ -179,6 +295,8 @@ k_tc_rf(const TcUnit *__restrict__ units, int n_units, int64_t n_items, int *cou
         unsigned char *B2 = B1 + (size_t)nN * K1 * 2;
         float4 *sc = reinterpret_cast<float4 *>(B2 + (size_t)nN * 256 * 2);
         SubElem *sub = reinterpret_cast<SubElem *>(sc + kSB);
+        float4 *tabs = reinterpret_cast<float4 *>(sub + M);               // delta table
+        const bool use_tab = !HAS_Y && gc.tab_n > 0;
         const uint32_t abuf0 = tc::smem_u32(A0), abuf1 = tc::smem_u32(A1);
         const uint32_t b1s = tc::smem_u32(B1), b2s = tc::smem_u32(B2);
         const uint32_t idesc1 = tc::idesc_f16(128, nN, BF16);
@@ -186,6 +304,8 @@ k_tc_rf(const TcUnit *__restrict__ units, int n_units, int64_t n_items, int *cou
         const uint32_t b1_bytes = (uint32_t)nN * K1 * 2;
         if (ui != cur_unit) {
             for (int i = tid; i < M; i += kThreads) sub[i] = U.sub[i];
+            if (use_tab)
+                for (int i = tid; i < gc.tab_n; i += kThreads) tabs[i] = U.dtab[i];
             cur_unit = ui;
             __syncthreads();
         }
@@ -224,45 +344,16 @@ k_tc_rf(const TcUnit *__restrict__ units, int n_units, int64_t n_items, int *cou
                 }
                 // ---- Green's tiles of bin kA (buffer 0) and kB (buffer 1): items (s, 8 elements)
                 const float qA = (float)(gc.q_lo + kA), qB = (float)(gc.q_lo + kB);
-                const int n_groups = Np >> 3;
-                for (int it = tid; it < kSB * n_groups; it += kThreads) {
-                    const int s = it & (kSB - 1), eg = it >> 7;
-                    const float4 ps = sc[s];
-                    float ar[8], ai[8], br[8], bi[8];
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const int e = eg * 8 + j;
-                        float xr = 0.f, xi = 0.f, yr = 0.f, yi = 0.f;
-                        if (e < N) {
-                            for (int mu = 0; mu < nu; ++mu) {
-                                const PairSetup pa =
-                                    pair_setup<HAS_Y, LINEAR>(gc, sub[e * nu + mu], ps.x, ps.y, ps.z, qA);
-                                const float2 g = green_term<HAS_Y, NARROW>(gc, pa, qA, pa.amp0);
-                                xr += g.x;
-                                xi += g.y;
-                                if (nb == 2) {
-                                    const float2 h = green_term<HAS_Y, NARROW>(gc, pa, qB, pa.amp0 * pa.mstep);
-                                    yr += h.x;
-                                    yi += h.y;
-                                }
-                            }
-                        }
-                        ar[j] = xr; ai[j] = xi; br[j] = yr; bi[j] = yi;
-                    }
-                    *reinterpret_cast<uint4 *>(A0 + tc::kmajor_offset(s, eg * 8, K1)) =
-                        make_uint4(h16x2<BF16>(ar[0], ar[1]), h16x2<BF16>(ar[2], ar[3]),
-                                   h16x2<BF16>(ar[4], ar[5]), h16x2<BF16>(ar[6], ar[7]));
-                    *reinterpret_cast<uint4 *>(A0 + tc::kmajor_offset(s, Np + eg * 8, K1)) =
-                        make_uint4(h16x2<BF16>(ai[0], ai[1]), h16x2<BF16>(ai[2], ai[3]),
-                                   h16x2<BF16>(ai[4], ai[5]), h16x2<BF16>(ai[6], ai[7]));
-                    if (nb == 2) {
-                        *reinterpret_cast<uint4 *>(A1 + tc::kmajor_offset(s, eg * 8, K1)) =
-                            make_uint4(h16x2<BF16>(br[0], br[1]), h16x2<BF16>(br[2], br[3]),
-                                       h16x2<BF16>(br[4], br[5]), h16x2<BF16>(br[6], br[7]));
-                        *reinterpret_cast<uint4 *>(A1 + tc::kmajor_offset(s, Np + eg * 8, K1)) =
-                            make_uint4(h16x2<BF16>(bi[0], bi[1]), h16x2<BF16>(bi[2], bi[3]),
-                                       h16x2<BF16>(bi[4], bi[5]), h16x2<BF16>(bi[6], bi[7]));
-                    }
+                if (nb == 2) {
+                    if (!HAS_Y && use_tab)
+                        gen_tiles<2, !HAS_Y, HAS_Y, BF16, NARROW, LINEAR>(gc, sub, tabs, sc, Np, qA, qB, A0, A1, tid);
+                    else
+                        gen_tiles<2, false, HAS_Y, BF16, NARROW, LINEAR>(gc, sub, tabs, sc, Np, qA, qB, A0, A1, tid);
+                } else {
+                    if (!HAS_Y && use_tab)
+                        gen_tiles<1, !HAS_Y, HAS_Y, BF16, NARROW, LINEAR>(gc, sub, tabs, sc, Np, qA, qB, A0, A1, tid);
+                    else
+                        gen_tiles<1, false, HAS_Y, BF16, NARROW, LINEAR>(gc, sub, tabs, sc, Np, qA, qB, A0, A1, tid);
                 }
                 tc::fence_proxy_async_smem();
                 tc::fence_before_sync();
@@ -405,21 +496,22 @@ TcShape tc_shape(const simus_plan *p, int T, int64_t S, double work_share, int i
     if (g.Np > 256) return g;
     g.mh = g.Np > 128 ? 2 : 1;
     const size_t limit = 227 * 1024 - kHeader - 1024;
+    const int tab_n = (p->delta_table && p->d_dtab) ? p->gc.tab_n : 0;
     // Two tile buffers (geometry shared by bin pairs) with at most two transmit groups,
     // else one buffer with the largest group that fits; tensor memory holds D1 and
     // QB * G * mh accumulator slices of nN columns.
-    for (int pair = 1; pair >= 0 && !g.ok; --pair) {
+    for (int pair = p->pair_mode ? 1 : 0; pair >= 0 && !g.ok; --pair) {
         for (int TG = std::min(T, 120); TG >= 1 && !g.ok; TG = (TG > 8 ? TG - 8 : TG - 1)) {
             const int nN = ((2 * TG + 15) / 16) * 16;
             const int G = (T + TG - 1) / TG;
             if (pair && G > 2) break;
             const int qb = (512 - nN) / (nN * G * g.mh);
             if (qb < (pair ? 2 : 1)) continue;
-            const size_t sm = unit_smem(g.Np, nN, pair, p->M);
+            const size_t sm = unit_smem(g.Np, nN, pair, p->M, tab_n);
             if (sm > limit) continue;
             g.ok = true;
             g.TG = TG; g.nN = nN; g.pair = pair; g.n_groups = G;
-            g.QB = std::min(4, qb);
+            g.QB = std::min(std::max(p->max_bins, pair ? 2 : 1), qb);
             if (pair && (g.QB & 1)) g.QB -= 1;
             g.smem = sm + kHeader;
         }
@@ -428,7 +520,9 @@ TcShape tc_shape(const simus_plan *p, int T, int64_t S, double work_share, int i
     g.n_btiles = (p->nq + g.QB - 1) / g.QB;
     g.n_tiles = std::max<int64_t>(1, (S + kSB - 1) / kSB);
     int64_t chunks;
-    if (work_share >= 0.999) {
+    if (work_share >= 0.999 && p->chunks > 0) {
+        chunks = std::min<int64_t>(p->chunks, g.n_tiles);
+    } else if (work_share >= 0.999) {
         // one simulation: the chunk count minimising the modelled makespan
         // ceil(items / SMs) * tiles per item, items = bin tiles * chunks
         const int64_t per = (int64_t)g.n_btiles;

@@ -257,6 +257,50 @@ GreenConst green_const(const simus_probe &pr, const simus_medium &md, int N, int
     return gc;
 }
 
+void plan_delta_table(simus_plan *p, std::vector<float4> &tab) {
+    // Eq. 15-16 at Y = 0 in the rescaled variable: delta/h = sum_g A_g sqrt(pi / (B_g + i x))
+    static const double Ar[4] = {0.187, 0.288, 0.187, 0.288}, Ai[4] = {0.275, -1.954, -0.275, 1.954};
+    static const double Br[4] = {4.558, 8.598, 4.558, 8.598}, Bi[4] = {-25.59, -7.924, 25.59, 7.924};
+    GreenConst &gc = p->gc;
+    gc.tab_n = 0;
+    tab.clear();
+    const double kx = M_PI * gc.df / p->medium.c * p->probe.height * p->probe.height;  // x per bin per (1/m)
+    const double inv_rf = std::isinf(p->probe.elev_focus) ? 0.0 : 1.0 / p->probe.elev_focus;
+    const double inv_r_max = 1.0 / 2e-3;
+    double xs[4] = {p->q_lo * kx * inv_rf, p->q_hi * kx * inv_rf,
+                    p->q_lo * kx * (inv_rf - inv_r_max), p->q_hi * kx * (inv_rf - inv_r_max)};
+    const double xlo = std::min(0.0, *std::min_element(xs, xs + 4));
+    const double xhi = std::max(0.0, *std::max_element(xs, xs + 4));
+    const double dx = 0.5;
+    const double x0 = std::floor(xlo) - 1.0;
+    const int n = (int)std::ceil((xhi - x0) / dx) + 3;
+    if (n > 4096) return;
+    tab.resize(n);
+    for (int j = 0; j < n; ++j) {
+        const double x = x0 + j * dx;
+        double fr = 0, fi = 0, dr = 0, di = 0;
+        for (int g = 0; g < 4; ++g) {
+            // a = B + i x; f += A sqrt(pi) a^{-1/2}; df/dx += A sqrt(pi) (-1/2) a^{-3/2} i
+            const double ar = Br[g], ai = Bi[g] + x;
+            const double m = std::hypot(ar, ai);
+            const double w = std::sqrt((m + ar) / 2.0), v = ai / (2.0 * w);      // sqrt(a) = w + i v
+            const double ir = w / m, ii = -v / m;                                // a^{-1/2}
+            const double pr = (ir * ar + ii * ai) / (m * m), pim = (ii * ar - ir * ai) / (m * m);  // a^{-3/2}
+            const double cr = Ar[g] * std::sqrt(M_PI), ci = Ai[g] * std::sqrt(M_PI);
+            fr += cr * ir - ci * ii;
+            fi += cr * ii + ci * ir;
+            // (-1/2) i a^{-3/2} = (0.5 pim, -0.5 pr)
+            const double qr = 0.5 * pim, qi = -0.5 * pr;
+            dr += cr * qr - ci * qi;
+            di += cr * qi + ci * qr;
+        }
+        tab[j] = make_float4((float)fr, (float)fi, (float)(dr * dx), (float)(di * dx));
+    }
+    gc.tab_n = n;
+    gc.tab_x0 = (float)x0;
+    gc.tab_inv_dx = (float)(1.0 / dx);
+}
+
 // The plan's tables: sub-element records (Eq. 24; convex: arc of radius R about (0, -R))
 // into sub[M], transfer values H_q = S_P S_T (Eq. 25-28, Eq. 34) into H[nq].
 void plan_fill_tables(const simus_plan *p, SubElem *sub, float2 *H) {
@@ -335,8 +379,13 @@ int simus_plan_create(const simus_probe *probe, const simus_medium *medium, int3
     std::vector<SubElem> sub(p->M);
     std::vector<float2> H(p->nq);
     plan_fill_tables(p, sub.data(), H.data());
+    std::vector<float4> dtab;
+    plan_delta_table(p, dtab);
 
     cudaError_t e = cudaGetDevice(&p->device);
+    if (e == cudaSuccess && !dtab.empty()) e = cudaMalloc(&p->d_dtab, sizeof(float4) * dtab.size());
+    if (e == cudaSuccess && !dtab.empty())
+        e = cudaMemcpy(p->d_dtab, dtab.data(), sizeof(float4) * dtab.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
     if (e == cudaSuccess) e = cudaMalloc(&p->d_sub, sizeof(SubElem) * p->M);
     if (e == cudaSuccess) e = cudaMalloc(&p->d_H, sizeof(float2) * p->nq);
@@ -367,6 +416,7 @@ void simus_plan_destroy(simus_plan *plan) {
     cudaFree(plan->d_sub);
     cudaFree(plan->d_H);
     cudaFree(plan->d_err);
+    cudaFree(plan->d_dtab);
     cudaFree(plan->d_work);
     cudaSetDevice(cur);
     delete plan;
@@ -399,6 +449,30 @@ int simus_plan_set_profiling(simus_plan *plan, int32_t enable) {
         }
     }
     plan->profiling = enable != 0;
+    return SIMUS_OK;
+}
+
+int simus_plan_set_tuning(simus_plan *plan, const simus_tuning *t) {
+    if (!plan || !t) return fail(SIMUS_ERR_ARG, "plan and tuning must not be NULL");
+    if (t->items_per_sm > 1024 || t->max_bins > 64 || t->chunks > 65536 || t->pair > 1 ||
+        t->delta_table > 1)
+        return fail(SIMUS_ERR_ARG, "tuning value out of range");
+    plan->items_per_sm = t->items_per_sm > 0 ? t->items_per_sm : 4;
+    plan->max_bins = t->max_bins > 0 ? t->max_bins : 4;
+    plan->pair_mode = t->pair >= 0 ? t->pair : 1;
+    plan->delta_table = t->delta_table >= 0 ? t->delta_table : 1;
+    plan->chunks = t->chunks > 0 ? t->chunks : 0;
+    return SIMUS_OK;
+}
+
+int simus_plan_get_tuning(const simus_plan *plan, simus_tuning *t) {
+    if (!plan || !t) return fail(SIMUS_ERR_ARG, "plan and tuning must not be NULL");
+    *t = simus_tuning{};
+    t->items_per_sm = plan->items_per_sm;
+    t->max_bins = plan->max_bins;
+    t->pair = plan->pair_mode;
+    t->delta_table = plan->delta_table;
+    t->chunks = plan->chunks;
     return SIMUS_OK;
 }
 
@@ -571,6 +645,8 @@ int tc_execute(simus_plan *owner, int n, simus_plan *const *plans, const simus_t
             TcUnit U{};
             U.gc = p->gc;
             U.sub = p->d_sub;
+            U.dtab = p->d_dtab;
+            if (!p->d_dtab || !p->delta_table) U.gc.tab_n = 0;
             U.x = scs[i].x; U.y = scs[i].y; U.z = scs[i].z; U.rc = scs[i].rc;
             U.delays = txs[i].delays; U.apod = txs[i].apod;
             U.S = scs[i].n; U.n_tiles = s.n_tiles;

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <vector>
 #include <cuda_runtime.h>
 
 #include "../../include/simus.h"
@@ -30,7 +31,9 @@ struct GreenConst {
     float h;          // element height (delta is evaluated as h * f(h^2 alpha))
     float h2;         // h^2
     int32_t narrow;   // 1 if |k b / nu| <= 3.2 at every kept bin (polynomial sinc suffices)
-    int32_t pad2_;
+    int32_t tab_n;    // entries of the delta table (0: none)
+    float tab_x0;     // delta table: first abscissa of x = h^2 (k/2)(1/R_f - 1/r)
+    float tab_inv_dx; // 1 / spacing
     double df;        // fs / nt [Hz]
 };
 
@@ -53,13 +56,18 @@ struct simus_plan {
     simus::SubElem *d_sub = nullptr;  // [M]
     float2 *d_H = nullptr;            // [nq] transfer S_P S_T at the kept bins
     int *d_err = nullptr;             // device-side error flag (bounded waits)
+    float4 *d_dtab = nullptr;         // [gc.tab_n] delta/h table (tensor-core path)
     void *d_work = nullptr;           // workspace
     size_t work_bytes = 0;
     void *h_stage = nullptr;          // pinned host staging of work descriptors
     size_t h_stage_bytes = 0;
     cudaEvent_t ev_stage = nullptr;   // recorded after the staging copy; guards reuse
     bool stage_pending = false;
-    int items_per_sm = 4;             // tensor-core path: work items per SM (tuning)
+    int items_per_sm = 4;             // tensor-core path tuning (simus_tuning)
+    int max_bins = 4;
+    int pair_mode = 1;
+    int delta_table = 1;
+    int chunks = 0;
     bool profiling = false;
     bool stage_used[SIMUS_N_STAGES] = {};
     cudaEvent_t ev[2 * SIMUS_N_STAGES] = {};
@@ -76,6 +84,10 @@ int workspace(simus_plan *plan, size_t bytes, void **ptr);
 int plan_setup_host(const simus_probe *probe, const simus_medium *medium, int32_t n_samples,
                     int32_t path, simus_plan *p);
 void plan_fill_tables(const simus_plan *p, SubElem *sub, float2 *H);
+// Cubic Hermite table of delta/h over the x = h^2 Im(alpha_g - B_g/h^2) reachable by the
+// plan's bins for scatterers at least 2 mm from a sub-element (spacing 0.5, relative error
+// <= 2.3e-6); sets gc.tab_x0, tab_inv_dx, tab_n (0 if it would exceed 4096 entries).
+void plan_delta_table(simus_plan *p, std::vector<float4> &tab);
 GreenConst green_const(const simus_probe &pr, const simus_medium &md, int N, int nu, double df,
                        double q_max);
 
@@ -132,6 +144,7 @@ TcShape tc_shape(const simus_plan *p, int T, int64_t S, double work_share, int i
 struct TcUnit {
     GreenConst gc;
     const SubElem *sub;
+    const float4 *dtab;           // delta/h table [gc.tab_n] (gc.tab_n = 0: direct evaluation)
     const float *x, *y, *z, *rc;
     const float *delays, *apod;   // of the whole simulation, [T][N]
     int64_t S, n_tiles;

@@ -60,6 +60,14 @@ class PlanInfo(C.Structure):
                 ("n_bins", C.c_int32), ("reserved", C.c_int32), ("df", C.c_double)]
 
 
+class Tuning(C.Structure):
+    _fields_ = [("items_per_sm", C.c_int32), ("max_bins", C.c_int32), ("pair", C.c_int32),
+                ("delta_table", C.c_int32), ("chunks", C.c_int32), ("reserved", C.c_int32 * 3)]
+
+
+TUNING_FIELDS = ("items_per_sm", "max_bins", "pair", "delta_table", "chunks")
+
+
 def _load():
     if not os.path.exists(_build.LIB):
         raise ImportError(f"CUDA library not built: {_build.LIB} is missing "
@@ -84,6 +92,8 @@ def _load():
     L.simus_last_error.restype = C.c_char_p
     L.simus_plan_set_profiling.argtypes = [vp, i32]
     L.simus_plan_get_timings.argtypes = [vp, C.POINTER(C.c_float)]
+    L.simus_plan_set_tuning.argtypes = [vp, C.POINTER(Tuning)]
+    L.simus_plan_get_tuning.argtypes = [vp, C.POINTER(Tuning)]
     L.simus_kernel_launches.restype = i64
     L.simus_kernel_launches.argtypes = []
     L.simus_plan_check.argtypes = [vp]
@@ -228,6 +238,23 @@ def simus_plan_get_timings(h) -> dict:
     return {name: float(v) for name, v in zip(STAGES, ms)}
 
 
+def simus_plan_set_tuning(h, **values):
+    """Set tensor-core launch shapes; fields not given keep their current value."""
+    t = Tuning()
+    _check(lib.simus_plan_get_tuning(h, t))
+    for k, v in values.items():
+        if k not in TUNING_FIELDS:
+            raise KeyError(k)
+        setattr(t, k, int(v))
+    _check(lib.simus_plan_set_tuning(h, t))
+
+
+def simus_plan_get_tuning(h) -> dict:
+    t = Tuning()
+    _check(lib.simus_plan_get_tuning(h, t))
+    return {k: int(getattr(t, k)) for k in TUNING_FIELDS}
+
+
 def simus_kernel_launches() -> int:
     return int(lib.simus_kernel_launches())
 
@@ -261,6 +288,12 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+    def set_tuning(self, **values):
+        simus_plan_set_tuning(self.handle, **values)
+
+    def get_tuning(self) -> dict:
+        return simus_plan_get_tuning(self.handle)
 
     @property
     def n_bins(self):

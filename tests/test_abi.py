@@ -53,6 +53,7 @@ int main(void) {
          sizeof(simus_scat), sizeof(simus_plan_info));
   printf("%zu %zu %zu %zu\n", offsetof(simus_probe, pitch), offsetof(simus_medium, pulse_cycles),
          offsetof(simus_tx, apod), offsetof(simus_plan_info, df));
+  printf("%zu %zu\n", sizeof(simus_tuning), offsetof(simus_tuning, chunks));
   return 0; }
 ''')
     exe = tmp_path / "layout"
@@ -60,7 +61,7 @@ int main(void) {
     out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
     got = [C.sizeof(S.Probe), C.sizeof(S.Medium), C.sizeof(S.Tx), C.sizeof(S.Scat),
            C.sizeof(S.PlanInfo), S.Probe.pitch.offset, S.Medium.pulse_cycles.offset,
-           S.Tx.apod.offset, S.PlanInfo.df.offset]
+           S.Tx.apod.offset, S.PlanInfo.df.offset, C.sizeof(S.Tuning), S.Tuning.chunks.offset]
     assert [int(v) for v in out] == got
 
 
@@ -88,3 +89,9 @@ def test_invalid_arguments_are_rejected_on_host(S, bad):
         S.simus_default_nt(cfg, 0.05, 0.0)
     assert ei.value.code == -1
     assert S.lib.simus_last_error().decode()
+
+
+def test_tuning_rejects_null_plan(S):
+    t = S.Tuning()
+    assert S.lib.simus_plan_set_tuning(None, t) == -1
+    assert S.lib.simus_plan_get_tuning(None, t) == -1

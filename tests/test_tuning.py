@@ -1,0 +1,108 @@
+"""The tensor-core path's tuning interface and the autotuner.
+
+Tunings change launch shapes only: every candidate must give the same RF as the FP64
+oracle within the tensor-core tolerance (2e-3 relative L2), and the direct and tabulated
+delta must agree to the table's error.  The autotuner must pick one of the timed
+candidates, set it on the plan and cache it under the problem's shape key.
+"""
+import json
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2102_02738_gb300 import phantoms as ph
+
+TOL_TC = 2e-3
+
+
+def test_candidates_cover_the_knobs():
+    from paper_2102_02738_gb300 import autotune
+    c = autotune.candidates(single=True)
+    assert {k for d in c for k in d} == {"max_bins", "pair", "delta_table", "chunks"}
+    assert {d["pair"] for d in c} == {0, 1} and {d["delta_table"] for d in c} == {0, 1}
+    cb = autotune.candidates(single=False)
+    assert {d["items_per_sm"] for d in cb} == {2, 4, 8}
+    assert autotune._bucket(1) == 1 and autotune._bucket(1000) == 1024 and autotune._bucket(1024) == 1024
+
+
+@pytest.fixture(scope="module")
+def S():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2102_02738_gb300 import build
+    build.build()
+    from paper_2102_02738_gb300 import simus
+    return simus
+
+
+def dev(a):
+    return None if a is None else torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+@pytest.mark.gpu
+def test_set_get_round_trip(S):
+    w = ph.tiny(n_elements=16, n_scat=50, n_tx=3)
+    plan = S.Plan(w.cfg, path="tc_f16")
+    assert plan.get_tuning() == dict(items_per_sm=4, max_bins=4, pair=1, delta_table=1, chunks=0)
+    plan.set_tuning(max_bins=6, pair=0, delta_table=0, chunks=3, items_per_sm=8)
+    assert plan.get_tuning() == dict(items_per_sm=8, max_bins=6, pair=0, delta_table=0, chunks=3)
+    plan.set_tuning(max_bins=-1, pair=-1, delta_table=-1, chunks=0, items_per_sm=-1)
+    assert plan.get_tuning() == dict(items_per_sm=4, max_bins=4, pair=1, delta_table=1, chunks=0)
+    with pytest.raises(S.SimusError):
+        plan.set_tuning(max_bins=65)
+    plan.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("tun", [dict(max_bins=2, pair=1, delta_table=1),
+                                 dict(max_bins=6, pair=1, delta_table=0, chunks=2),
+                                 dict(max_bins=3, pair=0, delta_table=1, chunks=1),
+                                 dict(max_bins=8, pair=0, delta_table=0)])
+def test_every_tuning_matches_the_oracle(S, oracle, tun):
+    w = ph.tiny(convex=True, n_elements=24, n_scat=400, n_tx=9)
+    ref = oracle.rf(w.cfg, w.delays, w.apod, w.x, w.y, w.z, w.rc)
+    plan = S.Plan(w.cfg, path="tc_f16")
+    plan.set_tuning(**tun)
+    got = plan.rf(*[dev(a) for a in (w.delays, w.apod, w.x, w.y, w.z, w.rc)]).cpu().numpy()
+    assert S.lib.simus_plan_check(plan.handle) == 0
+    plan.close()
+    assert rel_l2(got, ref) <= TOL_TC
+
+
+@pytest.mark.gpu
+def test_delta_table_agrees_with_direct_evaluation(S):
+    # same FP16 operands up to the table's 2.3e-6 relative error: far below FP16 rounding
+    w = ph.tiny(convex=True, n_elements=32, n_scat=600, n_tx=5)
+    args = [dev(a) for a in (w.delays, w.apod, w.x, w.y, w.z, w.rc)]
+    outs = []
+    for tab in (1, 0):
+        plan = S.Plan(w.cfg, path="tc_f16")
+        plan.set_tuning(delta_table=tab)
+        outs.append(plan.rf(*args).cpu().numpy())
+        plan.close()
+    assert rel_l2(outs[0], outs[1]) <= 2e-4
+
+
+@pytest.mark.gpu
+def test_autotuner_picks_and_caches(S, tmp_path):
+    from paper_2102_02738_gb300 import autotune
+    w = ph.tiny(n_elements=32, n_scat=700, n_tx=4)
+    args = [dev(a) for a in (w.delays, w.apod, w.x, w.y, w.z, w.rc)]
+    plan = S.Plan(w.cfg, path="tc_f16")
+    cache = tmp_path / "tune.json"
+    cands = [dict(max_bins=2, pair=1, delta_table=1, chunks=0), dict(max_bins=4, pair=0, delta_table=0, chunks=0)]
+    r = autotune.tune_rf(plan, *args, reps=1, cache_path=str(cache), cands=cands)
+    assert r["best"] in cands and len(r["all"]) == 2 and r["ms"] > 0
+    assert plan.get_tuning()["max_bins"] == r["best"]["max_bins"]
+    key = autotune.shape_key(plan, w.n_tx, w.n_scat)
+    assert key in json.loads(cache.read_text())
+    plan2 = S.Plan(w.cfg, path="tc_f16")
+    assert autotune.apply_cached(plan2, w.n_tx, w.n_scat, cache_path=str(cache))
+    assert plan2.get_tuning()["pair"] == r["best"]["pair"]
+    plan.close()
+    plan2.close()
