@@ -50,21 +50,11 @@ __device__ __forceinline__ uint32_t h16x2(float lo, float hi) {
     return (uint32_t)h16<BF16>(lo) | ((uint32_t)h16<BF16>(hi) << 16);
 }
 
-// delta / h from the cubic Hermite table at x (clamped into the table; `in` tells
-// whether x was inside, else the caller evaluates it directly).
-__device__ __forceinline__ float2 tab_delta(const float4 *__restrict__ tab, float x, float x0,
-                                            float inv_dx, int n, bool &in) {
-    float t = (x - x0) * inv_dx;
-    in = t >= 0.0f && t < (float)(n - 1);
-    t = fminf(fmaxf(t, 0.0f), (float)(n - 1) - 0.5f);
-    const float fl = floorf(t);
-    const int i = (int)fl;
-    const float u = t - fl, u2 = u * u, u3 = u2 * u;
-    const float h01 = fmaf(-2.0f, u3, 3.0f * u2), h00 = 1.0f - h01;
-    const float h11 = u3 - u2, h10 = h11 - u2 + u;
-    const float4 a = tab[i], b = tab[i + 1];
-    return make_float2(fmaf(h00, a.x, fmaf(h10, a.z, fmaf(h01, b.x, h11 * b.z))),
-                       fmaf(h00, a.y, fmaf(h10, a.w, fmaf(h01, b.y, h11 * b.w))));
+// delta / h from the table of cubic pieces: interval i holds c0..c3 (complex) of
+// c0 + c1 u + c2 u^2 + c3 u^3, u = t - i, t = (x - x0) / dx (two float4 per interval).
+__device__ __forceinline__ float2 cubic_piece(const float4 &lo, const float4 &hi, float u) {
+    return make_float2(fmaf(u, fmaf(u, fmaf(u, hi.z, hi.x), lo.z), lo.x),
+                       fmaf(u, fmaf(u, fmaf(u, hi.w, hi.y), lo.w), lo.y));
 }
 
 // Sub-element sums (Eq. 33) of the Green's terms of elements e0 and e0 + 1 for one
@@ -79,6 +69,7 @@ __device__ __forceinline__ void gen_two(const GreenConst &gc, const SubElem *sub
     const int N = gc.N, nu = gc.nu;
     const float w0 = e0 < N ? 1.0f : 0.0f, w1 = e0 + 1 < N ? 1.0f : 0.0f;
     const int b0 = min(e0, N - 1) * nu, b1 = min(e0 + 1, N - 1) * nu;
+    const float t0 = gc.tab_x0 * gc.tab_inv_dx, tmax = (float)gc.tab_n - 0.5f;
 #pragma unroll
     for (int c = 0; c < 2; ++c)
 #pragma unroll
@@ -91,7 +82,7 @@ __device__ __forceinline__ void gen_two(const GreenConst &gc, const SubElem *sub
         P[1].amp0 *= w1;
         float er[2][NB], ei[2][NB];
         float2 d[2][NB];
-        bool in_all = true;
+        bool ok = true;
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
             const float q = b ? qB : qA;
@@ -104,24 +95,34 @@ __device__ __forceinline__ void gen_two(const GreenConst &gc, const SubElem *sub
                 const float m = amp * sinc_f<NARROW>(q * P[c].xb);
                 er[c][b] = cs * m;
                 ei[c][b] = sn * m;
-                if (TAB) {
-                    bool in;
-                    d[c][b] = tab_delta(tabs, q * P[c].kap, gc.tab_x0, gc.tab_inv_dx, gc.tab_n, in);
-                    in_all = in_all && in;
-                } else {
-                    d[c][b] = delta_f<HAS_Y>(gc, P[c], q);
-                }
+                if (!TAB) d[c][b] = delta_f<HAS_Y>(gc, P[c], q);
             }
         }
-        if (TAB && !in_all) {   // rare: x outside the table (a scatterer within 2 mm)
+        if (TAB) {
+            // bin qA picks the interval; qB = qA + 1 moves u by kap / dx (small beyond a
+            // few mm) and reuses the same piece, extrapolated by at most a quarter interval
 #pragma unroll
-            for (int b = 0; b < NB; ++b)
-#pragma unroll
-                for (int c = 0; c < 2; ++c) {
-                    const float q = b ? qB : qA;
-                    const float t = (q * P[c].kap - gc.tab_x0) * gc.tab_inv_dx;
-                    if (!(t >= 0.0f && t < (float)(gc.tab_n - 1))) d[c][b] = delta_f<false>(gc, P[c], q);
+            for (int c = 0; c < 2; ++c) {
+                const float kt = P[c].kap * gc.tab_inv_dx;
+                const float t = fmaf(qA, kt, -t0);
+                const float fl = floorf(fminf(fmaxf(t, 0.0f), tmax));
+                const int i = (int)fl;
+                const float u = t - fl;
+                const float4 lo = tabs[2 * i], hi = tabs[2 * i + 1];
+                d[c][0] = cubic_piece(lo, hi, u);
+                ok = ok && u >= 0.0f && u <= 1.0f;
+                if (NB == 2) {
+                    const float u2 = u + kt;
+                    d[c][NB - 1] = cubic_piece(lo, hi, u2);
+                    ok = ok && u2 >= -0.25f && u2 <= 1.25f;
                 }
+            }
+            if (!ok) {   // rare: a scatterer within ~2 mm of the sub-element
+#pragma unroll
+                for (int c = 0; c < 2; ++c)
+#pragma unroll
+                    for (int b = 0; b < NB; ++b) d[c][b] = delta_f<false>(gc, P[c], b ? qB : qA);
+            }
         }
 #pragma unroll
         for (int b = 0; b < NB; ++b)
@@ -170,7 +171,7 @@ __device__ __forceinline__ void gen_tiles(const GreenConst &gc, const SubElem *s
 size_t unit_smem(int Np, int nN, int pair, int M, int tab_n) {
     const size_t a = (size_t)kSB * 2 * Np * 2;
     return (pair ? 2 : 1) * a + (size_t)nN * 2 * Np * 2 + (size_t)nN * 256 * 2
-         + sizeof(float4) * kSB + sizeof(SubElem) * M + sizeof(float4) * tab_n;
+         + sizeof(float4) * kSB + sizeof(SubElem) * M + 2 * sizeof(float4) * tab_n;
 }
 }  // namespace
 
@@ -305,7 +306,7 @@ k_tc_rf(const TcUnit *__restrict__ units, int n_units, int64_t n_items, int *cou
         if (ui != cur_unit) {
             for (int i = tid; i < M; i += kThreads) sub[i] = U.sub[i];
             if (use_tab)
-                for (int i = tid; i < gc.tab_n; i += kThreads) tabs[i] = U.dtab[i];
+                for (int i = tid; i < 2 * gc.tab_n; i += kThreads) tabs[i] = U.dtab[i];
             cur_unit = ui;
             __syncthreads();
         }
@@ -496,11 +497,14 @@ TcShape tc_shape(const simus_plan *p, int T, int64_t S, double work_share, int i
     if (g.Np > 256) return g;
     g.mh = g.Np > 128 ? 2 : 1;
     const size_t limit = 227 * 1024 - kHeader - 1024;
-    const int tab_n = (p->delta_table && p->d_dtab) ? p->gc.tab_n : 0;
+    const int tab_full = (p->delta_table && p->d_dtab) ? p->gc.tab_n : 0;
     // Two tile buffers (geometry shared by bin pairs) with at most two transmit groups,
-    // else one buffer with the largest group that fits; tensor memory holds D1 and
-    // QB * G * mh accumulator slices of nN columns.
-    for (int pair = p->pair_mode ? 1 : 0; pair >= 0 && !g.ok; --pair) {
+    // else one buffer with the largest group that fits; the delta table where it still
+    // fits beside them; tensor memory holds D1 and QB * G * mh accumulator slices of nN
+    // columns.
+    for (int opt = 0; opt < 4 && !g.ok; ++opt) {
+        const int pair = (opt < 2 && p->pair_mode) ? 1 : 0;
+        const int tab_n = (opt & 1) ? 0 : tab_full;
         for (int TG = std::min(T, 120); TG >= 1 && !g.ok; TG = (TG > 8 ? TG - 8 : TG - 1)) {
             const int nN = ((2 * TG + 15) / 16) * 16;
             const int G = (T + TG - 1) / TG;
@@ -510,7 +514,7 @@ TcShape tc_shape(const simus_plan *p, int T, int64_t S, double work_share, int i
             const size_t sm = unit_smem(g.Np, nN, pair, p->M, tab_n);
             if (sm > limit) continue;
             g.ok = true;
-            g.TG = TG; g.nN = nN; g.pair = pair; g.n_groups = G;
+            g.TG = TG; g.nN = nN; g.pair = pair; g.n_groups = G; g.tab_n = tab_n;
             g.QB = std::min(std::max(p->max_bins, pair ? 2 : 1), qb);
             if (pair && (g.QB & 1)) g.QB -= 1;
             g.smem = sm + kHeader;

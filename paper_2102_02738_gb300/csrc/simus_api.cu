@@ -273,9 +273,9 @@ void plan_delta_table(simus_plan *p, std::vector<float4> &tab) {
     const double xhi = std::max(0.0, *std::max_element(xs, xs + 4));
     const double dx = 0.5;
     const double x0 = std::floor(xlo) - 1.0;
-    const int n = (int)std::ceil((xhi - x0) / dx) + 3;
-    if (n > 4096) return;
-    tab.resize(n);
+    int n = (int)std::ceil((xhi - x0) / dx) + 3;   // nodes; n - 1 intervals
+    if (n > 2049) return;
+    std::vector<double> f(4 * n);   // per node: Re f, Im f, Re f' dx, Im f' dx
     for (int j = 0; j < n; ++j) {
         const double x = x0 + j * dx;
         double fr = 0, fi = 0, dr = 0, di = 0;
@@ -294,8 +294,25 @@ void plan_delta_table(simus_plan *p, std::vector<float4> &tab) {
             dr += cr * qr - ci * qi;
             di += cr * qi + ci * qr;
         }
-        tab[j] = make_float4((float)fr, (float)fi, (float)(dr * dx), (float)(di * dx));
+        f[4 * j] = fr; f[4 * j + 1] = fi; f[4 * j + 2] = dr * dx; f[4 * j + 3] = di * dx;
     }
+    // interval j: the cubic Hermite interpolant in u = (x - x_j) / dx as power-basis
+    // coefficients c0 + c1 u + c2 u^2 + c3 u^3 (complex), two float4 per interval
+    tab.resize(2 * (n - 1));
+    for (int j = 0; j + 1 < n; ++j) {
+        double c[4][2];
+        for (int k = 0; k < 2; ++k) {
+            const double f0 = f[4 * j + k], f1 = f[4 * j + 4 + k];
+            const double d0 = f[4 * j + 2 + k], d1 = f[4 * j + 6 + k];
+            c[0][k] = f0;
+            c[1][k] = d0;
+            c[2][k] = 3.0 * (f1 - f0) - 2.0 * d0 - d1;
+            c[3][k] = 2.0 * (f0 - f1) + d0 + d1;
+        }
+        tab[2 * j] = make_float4((float)c[0][0], (float)c[0][1], (float)c[1][0], (float)c[1][1]);
+        tab[2 * j + 1] = make_float4((float)c[2][0], (float)c[2][1], (float)c[3][0], (float)c[3][1]);
+    }
+    n = n - 1;
     gc.tab_n = n;
     gc.tab_x0 = (float)x0;
     gc.tab_inv_dx = (float)(1.0 / dx);
@@ -646,7 +663,7 @@ int tc_execute(simus_plan *owner, int n, simus_plan *const *plans, const simus_t
             U.gc = p->gc;
             U.sub = p->d_sub;
             U.dtab = p->d_dtab;
-            if (!p->d_dtab || !p->delta_table) U.gc.tab_n = 0;
+            U.gc.tab_n = s.tab_n;
             U.x = scs[i].x; U.y = scs[i].y; U.z = scs[i].z; U.rc = scs[i].rc;
             U.delays = txs[i].delays; U.apod = txs[i].apod;
             U.S = scs[i].n; U.n_tiles = s.n_tiles;

@@ -31,7 +31,7 @@ struct GreenConst {
     float h;          // element height (delta is evaluated as h * f(h^2 alpha))
     float h2;         // h^2
     int32_t narrow;   // 1 if |k b / nu| <= 3.2 at every kept bin (polynomial sinc suffices)
-    int32_t tab_n;    // entries of the delta table (0: none)
+    int32_t tab_n;    // intervals of the delta table (0: none)
     float tab_x0;     // delta table: first abscissa of x = h^2 (k/2)(1/R_f - 1/r)
     float tab_inv_dx; // 1 / spacing
     double df;        // fs / nt [Hz]
@@ -56,7 +56,7 @@ struct simus_plan {
     simus::SubElem *d_sub = nullptr;  // [M]
     float2 *d_H = nullptr;            // [nq] transfer S_P S_T at the kept bins
     int *d_err = nullptr;             // device-side error flag (bounded waits)
-    float4 *d_dtab = nullptr;         // [gc.tab_n] delta/h table (tensor-core path)
+    float4 *d_dtab = nullptr;         // [2 gc.tab_n] delta/h cubic pieces (tensor-core path)
     void *d_work = nullptr;           // workspace
     size_t work_bytes = 0;
     void *h_stage = nullptr;          // pinned host staging of work descriptors
@@ -86,7 +86,8 @@ int plan_setup_host(const simus_probe *probe, const simus_medium *medium, int32_
 void plan_fill_tables(const simus_plan *p, SubElem *sub, float2 *H);
 // Cubic Hermite table of delta/h over the x = h^2 Im(alpha_g - B_g/h^2) reachable by the
 // plan's bins for scatterers at least 2 mm from a sub-element (spacing 0.5, relative error
-// <= 2.3e-6); sets gc.tab_x0, tab_inv_dx, tab_n (0 if it would exceed 4096 entries).
+// <= 2.3e-6), as power-basis pieces (two float4 per interval); sets gc.tab_x0, tab_inv_dx,
+// tab_n = intervals (0 if it would exceed 2048).
 void plan_delta_table(simus_plan *p, std::vector<float4> &tab);
 GreenConst green_const(const simus_probe &pr, const simus_medium &md, int N, int nu, double df,
                        double q_max);
@@ -130,6 +131,7 @@ struct TcShape {
     int nN;              // GEMM N of a group: 2 TG padded to 16
     int mh;              // receive GEMM M-halves: 1 (Np <= 128) or 2
     int pair;            // 1: bins generated in pairs into two tile buffers
+    int tab_n;           // delta-table intervals staged in shared memory (0: direct delta)
     int QB;              // bins per work item
     int n_btiles;
     int64_t n_tiles;     // scatterer tiles of 128
@@ -144,7 +146,7 @@ TcShape tc_shape(const simus_plan *p, int T, int64_t S, double work_share, int i
 struct TcUnit {
     GreenConst gc;
     const SubElem *sub;
-    const float4 *dtab;           // delta/h table [gc.tab_n] (gc.tab_n = 0: direct evaluation)
+    const float4 *dtab;           // delta/h cubic pieces [2 gc.tab_n] (gc.tab_n = 0: direct)
     const float *x, *y, *z, *rc;
     const float *delays, *apod;   // of the whole simulation, [T][N]
     int64_t S, n_tiles;
