@@ -212,15 +212,16 @@ int simus_plan_get_timings(simus_plan *plan, float *ms);
  *   items_per_sm  batches: work items per SM the scatterer chunking aims at (default 4)
  *   max_bins      frequency bins per work item, upper bound (default 4; tensor memory
  *                 may allow fewer)
- *   pair          1: bins generated two at a time into two tile buffers where shared
- *                 memory allows (default), 0: one buffer
+ *   pair          bins generated per pass from one geometry setup, minus one: 2 three
+ *                 (two shared-memory tile buffers and a tensor-memory stash; default),
+ *                 1 two (two buffers), 0 one; the largest that fits at most this
  *   delta_table   1: delta from the table where Y = 0 (default), 0: direct evaluation
  *   chunks        single simulations: scatterer chunks per bin tile (default: chosen by a
  *                 makespan model over the SMs)
  * The project's autotuner (paper_2102_02738_gb300/autotune.py) times candidates through
  * these calls and caches the fastest per problem shape.
  * Returns SIMUS_ERR_ARG for a NULL plan or values out of range (max_bins > 64,
- * items_per_sm > 1024, chunks > 65536). */
+ * items_per_sm > 1024, chunks > 65536, pair > 2, delta_table > 1). */
 typedef struct simus_tuning {
     int32_t items_per_sm;
     int32_t max_bins;

@@ -39,7 +39,7 @@ def candidates(single: bool = True):
     batches).  Chunk counts are left to the library's makespan model, plus two fixed
     alternatives around it for single simulations."""
     out = []
-    for mb, pair, tab in itertools.product((2, 4, 6, 8), (1, 0), (1, 0)):
+    for mb, pair, tab in itertools.product((2, 3, 4, 6), (2, 1, 0), (1, 0)):
         if single:
             out.append(dict(max_bins=mb, pair=pair, delta_table=tab, chunks=0))
         else:

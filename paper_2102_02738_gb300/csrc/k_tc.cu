@@ -58,14 +58,17 @@ __device__ __forceinline__ float2 cubic_piece(const float4 &lo, const float4 &hi
 }
 
 // Sub-element sums (Eq. 33) of the Green's terms of elements e0 and e0 + 1 for one
-// scatterer at bins qA (and qB = qA + 1 when NB = 2): two independent evaluation chains
-// side by side, so that each warp has twice the instruction-level parallelism.  An
-// element past N is evaluated on element N - 1 with zero amplitude (no branch).
-// o[c][b] = (Re, Im) of element e0 + c at bin b.
+// scatterer at the NB consecutive bins qA, qA + 1, ...: two independent evaluation chains
+// side by side, so that each warp has twice the instruction-level parallelism, and one
+// geometry setup per (scatterer, sub-element) for all NB bins.  An element past N is
+// evaluated on element N - 1 with zero amplitude (no branch).  With the delta table, bin
+// qA picks the cubic piece and the later bins reuse it: bin qA + b moves u by b kap/dx,
+// small except within a few mm of the sub-element, where (|u| check) delta is evaluated
+// directly instead.  o[c][b] = (Re, Im) of element e0 + c at bin qA + b.
 template <int NB, bool TAB, bool HAS_Y, bool NARROW, bool LINEAR>
 __device__ __forceinline__ void gen_two(const GreenConst &gc, const SubElem *sub,
                                         const float4 *tabs, const float4 &ps, int e0, float qA,
-                                        float qB, float (&o)[2][NB][2]) {
+                                        float (&o)[2][NB][2]) {
     const int N = gc.N, nu = gc.nu;
     const float w0 = e0 < N ? 1.0f : 0.0f, w1 = e0 + 1 < N ? 1.0f : 0.0f;
     const int b0 = min(e0, N - 1) * nu, b1 = min(e0 + 1, N - 1) * nu;
@@ -80,49 +83,56 @@ __device__ __forceinline__ void gen_two(const GreenConst &gc, const SubElem *sub
         P[1] = pair_setup_f32<HAS_Y, LINEAR>(gc, sub[b1 + mu], ps.x, ps.y, ps.z, qA);
         P[0].amp0 *= w0;
         P[1].amp0 *= w1;
+        float kt[2] = {0.0f, 0.0f}, u[2] = {0.0f, 0.0f};
+        int ti[2] = {0, 0};
+        bool ok = TAB;
+        if (TAB) {
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                kt[c] = P[c].kap * gc.tab_inv_dx;
+                const float t = fmaf(qA, kt[c], -t0);
+                const float fl = floorf(fminf(fmaxf(t, 0.0f), tmax));
+                ti[c] = (int)fl;
+                u[c] = t - fl;
+                const float ue = fmaf((float)(NB - 1), kt[c], u[c]);
+                ok = ok && u[c] >= 0.0f && u[c] <= 1.0f && ue >= -0.25f && ue <= 1.25f;
+            }
+        }
+        float4 lo[2], hi[2];            // the pieces (index clamped: always a valid load)
+        if (TAB) {
+#pragma unroll
+            for (int c = 0; c < 2; ++c) { lo[c] = tabs[2 * ti[c]]; hi[c] = tabs[2 * ti[c] + 1]; }
+        }
+        // phase, absorption and sinc directivity of every bin (common to both delta forms)
         float er[2][NB], ei[2][NB];
-        float2 d[2][NB];
-        bool ok = true;
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
-            const float q = b ? qB : qA;
+            const float q = qA + (float)b;
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
                 const float fr = df_frac_mul(q, P[c].u);
                 float sn, cs;
                 sincos_a(6.283185307179586f * fr, sn, cs);
-                const float amp = b ? P[c].amp0 * P[c].mstep : P[c].amp0;
+                float amp = P[c].amp0;
+                if (b >= 1) amp *= P[c].mstep;
+                if (b >= 2) amp *= P[c].mstep;
                 const float m = amp * sinc_f<NARROW>(q * P[c].xb);
                 er[c][b] = cs * m;
                 ei[c][b] = sn * m;
-                if (!TAB) d[c][b] = delta_f<HAS_Y>(gc, P[c], q);
             }
         }
+        float2 d[2][NB];
         if (TAB) {
-            // bin qA picks the interval; qB = qA + 1 moves u by kap / dx (small beyond a
-            // few mm) and reuses the same piece, extrapolated by at most a quarter interval
 #pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                const float kt = P[c].kap * gc.tab_inv_dx;
-                const float t = fmaf(qA, kt, -t0);
-                const float fl = floorf(fminf(fmaxf(t, 0.0f), tmax));
-                const int i = (int)fl;
-                const float u = t - fl;
-                const float4 lo = tabs[2 * i], hi = tabs[2 * i + 1];
-                d[c][0] = cubic_piece(lo, hi, u);
-                ok = ok && u >= 0.0f && u <= 1.0f;
-                if (NB == 2) {
-                    const float u2 = u + kt;
-                    d[c][NB - 1] = cubic_piece(lo, hi, u2);
-                    ok = ok && u2 >= -0.25f && u2 <= 1.25f;
-                }
-            }
-            if (!ok) {   // rare: a scatterer within ~2 mm of the sub-element
+            for (int c = 0; c < 2; ++c)
 #pragma unroll
-                for (int c = 0; c < 2; ++c)
+                for (int b = 0; b < NB; ++b) d[c][b] = cubic_piece(lo[c], hi[c], fmaf((float)b, kt[c], u[c]));
+        }
+        if (!ok) {
 #pragma unroll
-                    for (int b = 0; b < NB; ++b) d[c][b] = delta_f<false>(gc, P[c], b ? qB : qA);
-            }
+            for (int c = 0; c < 2; ++c)
+#pragma unroll
+                for (int b = 0; b < NB; ++b) d[c][b] = delta_f<HAS_Y>(gc, P[c], qA + (float)b);
         }
 #pragma unroll
         for (int b = 0; b < NB; ++b)
@@ -134,36 +144,66 @@ __device__ __forceinline__ void gen_two(const GreenConst &gc, const SubElem *sub
     }
 }
 
-// One generation pass over a scatterer tile: every (scatterer, group of 8 elements)
-// item, written as FP16/BF16 rows of the K-major tile(s) A0 (bin qA) and A1 (bin qB).
+// One generation pass over a scatterer tile: every (scatterer, group of 8 elements) item
+// at bins qA .. qA + NB - 1, written as FP16/BF16 rows of the K-major tiles A0 (bin qA)
+// and A1 (bin qA + 1); a third bin goes to tensor memory (its row s in lane s, Re of the
+// 8 elements packed in columns st + 4 eg .. + 3, Im at st + Np/2 + 4 eg) until A0 is free.
+// The lane rule holds by construction: item it has s = it mod 128 = 32 (warp mod 4) + lane.
 template <int NB, bool TAB, bool HAS_Y, bool BF16, bool NARROW, bool LINEAR>
 __device__ __forceinline__ void gen_tiles(const GreenConst &gc, const SubElem *sub,
                                           const float4 *tabs, const float4 *sc, int Np,
-                                          float qA, float qB, unsigned char *A0,
-                                          unsigned char *A1, int tid) {
+                                          float qA, unsigned char *A0, unsigned char *A1,
+                                          uint32_t stash, int tid) {
     const int K1 = 2 * Np;
     const int n_groups = Np >> 3;
     for (int it = tid; it < kSB * n_groups; it += kThreads) {
         const int s = it & (kSB - 1), eg = it >> 7;
         const float4 ps = sc[s];
-        uint32_t pr[4], pi[4], qr[4], qi[4];
+        uint32_t pk[NB][2][4];
 #pragma unroll
         for (int jp = 0; jp < 4; ++jp) {
             float o[2][NB][2];
-            gen_two<NB, TAB, HAS_Y, NARROW, LINEAR>(gc, sub, tabs, ps, eg * 8 + 2 * jp, qA, qB, o);
-            pr[jp] = h16x2<BF16>(o[0][0][0], o[1][0][0]);
-            pi[jp] = h16x2<BF16>(o[0][0][1], o[1][0][1]);
-            if (NB == 2) {
-                qr[jp] = h16x2<BF16>(o[0][NB - 1][0], o[1][NB - 1][0]);
-                qi[jp] = h16x2<BF16>(o[0][NB - 1][1], o[1][NB - 1][1]);
+            gen_two<NB, TAB, HAS_Y, NARROW, LINEAR>(gc, sub, tabs, ps, eg * 8 + 2 * jp, qA, o);
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                pk[b][0][jp] = h16x2<BF16>(o[0][b][0], o[1][b][0]);
+                pk[b][1][jp] = h16x2<BF16>(o[0][b][1], o[1][b][1]);
             }
         }
-        *reinterpret_cast<uint4 *>(A0 + tc::kmajor_offset(s, eg * 8, K1)) = make_uint4(pr[0], pr[1], pr[2], pr[3]);
-        *reinterpret_cast<uint4 *>(A0 + tc::kmajor_offset(s, Np + eg * 8, K1)) = make_uint4(pi[0], pi[1], pi[2], pi[3]);
-        if (NB == 2) {
-            *reinterpret_cast<uint4 *>(A1 + tc::kmajor_offset(s, eg * 8, K1)) = make_uint4(qr[0], qr[1], qr[2], qr[3]);
-            *reinterpret_cast<uint4 *>(A1 + tc::kmajor_offset(s, Np + eg * 8, K1)) = make_uint4(qi[0], qi[1], qi[2], qi[3]);
+        *reinterpret_cast<uint4 *>(A0 + tc::kmajor_offset(s, eg * 8, K1)) =
+            make_uint4(pk[0][0][0], pk[0][0][1], pk[0][0][2], pk[0][0][3]);
+        *reinterpret_cast<uint4 *>(A0 + tc::kmajor_offset(s, Np + eg * 8, K1)) =
+            make_uint4(pk[0][1][0], pk[0][1][1], pk[0][1][2], pk[0][1][3]);
+        if (NB >= 2) {
+            *reinterpret_cast<uint4 *>(A1 + tc::kmajor_offset(s, eg * 8, K1)) =
+                make_uint4(pk[NB > 1][0][0], pk[NB > 1][0][1], pk[NB > 1][0][2], pk[NB > 1][0][3]);
+            *reinterpret_cast<uint4 *>(A1 + tc::kmajor_offset(s, Np + eg * 8, K1)) =
+                make_uint4(pk[NB > 1][1][0], pk[NB > 1][1][1], pk[NB > 1][1][2], pk[NB > 1][1][3]);
         }
+        if (NB == 3) {
+            const uint32_t ta = stash + ((uint32_t)(s & ~31) << 16) + 4u * eg;
+            tc::tmem_st4(ta, pk[NB - 1][0][0], pk[NB - 1][0][1], pk[NB - 1][0][2], pk[NB - 1][0][3]);
+            tc::tmem_st4(ta + (uint32_t)(Np >> 1), pk[NB - 1][1][0], pk[NB - 1][1][1], pk[NB - 1][1][2],
+                         pk[NB - 1][1][3]);
+        }
+    }
+    if (NB == 3) tc::tmem_wait_st();
+}
+
+// Move the stashed third bin from tensor memory into tile buffer A (same item-to-thread
+// map as gen_tiles, so every thread reads back the lanes and columns it wrote).
+__device__ __forceinline__ void unstash_tile(int Np, unsigned char *A, uint32_t stash, int tid) {
+    const int K1 = 2 * Np;
+    const int n_groups = Np >> 3;
+    for (int it = tid; it < kSB * n_groups; it += kThreads) {
+        const int s = it & (kSB - 1), eg = it >> 7;
+        const uint32_t ta = stash + ((uint32_t)(s & ~31) << 16) + 4u * eg;
+        uint32_t re[4], im[4];
+        tc::tmem_ld4(ta, re);
+        tc::tmem_ld4(ta + (uint32_t)(Np >> 1), im);
+        tc::tmem_wait_ld();
+        *reinterpret_cast<uint4 *>(A + tc::kmajor_offset(s, eg * 8, K1)) = make_uint4(re[0], re[1], re[2], re[3]);
+        *reinterpret_cast<uint4 *>(A + tc::kmajor_offset(s, Np + eg * 8, K1)) = make_uint4(im[0], im[1], im[2], im[3]);
     }
 }
 
@@ -323,13 +363,13 @@ k_tc_rf(const TcUnit *__restrict__ units, int n_units, int64_t n_items, int *cou
         const int k0 = bt * QB;
         const int64_t tile0 = (int64_t)chunk * U.tiles_per_chunk;
         const int64_t tile1 = std::min<int64_t>(tile0 + U.tiles_per_chunk, U.n_tiles);
-        const int step = pair ? 2 : 1;
+        const int step = pair + 1;                        // bins per generation pass
+        const uint32_t stash = tmem + (uint32_t)(nN * (1 + QB * G * mh));   // third bin's tile
         for (int64_t tile = tile0; tile < tile1 && !aborted; ++tile) {
             for (int bp = 0; bp < QB && !aborted; bp += step) {
                 const int nb = min(step, QB - bp);
-                const int kA = min(k0 + bp, nq - 1);       // bins past the end repeat the last
-                const int kB = min(k0 + bp + 1, nq - 1);   // (their outputs are discarded)
-                issue_b1(kA, 0);
+                const int kA = min(k0 + bp, nq - 1);   // bins past the end repeat the last
+                issue_b1(kA, 0);                        // (their outputs are discarded)
                 if (pending2) {   // tile buffers and B2 still read by the last MMA2
                     if (!wait_all(mbar2, ph2)) { aborted = true; break; }
                     ph2 ^= 1;
@@ -343,29 +383,38 @@ k_tc_rf(const TcUnit *__restrict__ units, int n_units, int64_t n_items, int *cou
                     }
                     __syncthreads();
                 }
-                // ---- Green's tiles of bin kA (buffer 0) and kB (buffer 1): items (s, 8 elements)
-                const float qA = (float)(gc.q_lo + kA), qB = (float)(gc.q_lo + kB);
-                if (nb == 2) {
-                    if (!HAS_Y && use_tab)
-                        gen_tiles<2, !HAS_Y, HAS_Y, BF16, NARROW, LINEAR>(gc, sub, tabs, sc, Np, qA, qB, A0, A1, tid);
-                    else
-                        gen_tiles<2, false, HAS_Y, BF16, NARROW, LINEAR>(gc, sub, tabs, sc, Np, qA, qB, A0, A1, tid);
+                // ---- Green's tiles of bins kA (buffer A0), kA + 1 (A1), kA + 2 (stash)
+                const float qA = (float)(gc.q_lo + kA);
+                const bool tab = !HAS_Y && use_tab;
+                if (nb == 3) {
+                    if (tab) gen_tiles<3, !HAS_Y, HAS_Y, BF16, NARROW, LINEAR>(gc, sub, tabs, sc, Np, qA, A0, A1, stash, tid);
+                    else gen_tiles<3, false, HAS_Y, BF16, NARROW, LINEAR>(gc, sub, tabs, sc, Np, qA, A0, A1, stash, tid);
+                } else if (nb == 2) {
+                    if (tab) gen_tiles<2, !HAS_Y, HAS_Y, BF16, NARROW, LINEAR>(gc, sub, tabs, sc, Np, qA, A0, A1, stash, tid);
+                    else gen_tiles<2, false, HAS_Y, BF16, NARROW, LINEAR>(gc, sub, tabs, sc, Np, qA, A0, A1, stash, tid);
                 } else {
-                    if (!HAS_Y && use_tab)
-                        gen_tiles<1, !HAS_Y, HAS_Y, BF16, NARROW, LINEAR>(gc, sub, tabs, sc, Np, qA, qB, A0, A1, tid);
-                    else
-                        gen_tiles<1, false, HAS_Y, BF16, NARROW, LINEAR>(gc, sub, tabs, sc, Np, qA, qB, A0, A1, tid);
+                    if (tab) gen_tiles<1, !HAS_Y, HAS_Y, BF16, NARROW, LINEAR>(gc, sub, tabs, sc, Np, qA, A0, A1, stash, tid);
+                    else gen_tiles<1, false, HAS_Y, BF16, NARROW, LINEAR>(gc, sub, tabs, sc, Np, qA, A0, A1, stash, tid);
                 }
                 tc::fence_proxy_async_smem();
                 tc::fence_before_sync();
                 __syncthreads();
                 tc::fence_after_sync();
 
-                // every bin of the pair, every transmit group: MMA1 -> P' -> MMA2
+                // every bin of the pass, every transmit group: MMA1 -> P' -> MMA2
                 for (int si = 0; si < nb * G && !aborted; ++si) {
                     const int bi_ = si / G, g = si - bi_ * G;
                     const int TGg = min(TG, T - g * TG);      // transmits of this group
-                    const uint32_t abase = bi_ ? abuf1 : abuf0;
+                    const uint32_t abase = bi_ == 1 ? abuf1 : abuf0;
+                    if (bi_ == 2 && g == 0) {
+                        // the third bin into A0: every MMA2 of the first bin (the last
+                        // readers of A0) completed before the second bin's first P'
+                        unstash_tile(Np, A0, stash, tid);
+                        tc::fence_proxy_async_smem();
+                        tc::fence_before_sync();
+                        __syncthreads();
+                        tc::fence_after_sync();
+                    }
                     // ---- MMA1: D1 = A * B1^T
                     if (tid == 0) {
                         if (!tc::mbar_wait_bounded(mbar_b1, ph_b1, kMaxWait)) {
@@ -387,7 +436,7 @@ k_tc_rf(const TcUnit *__restrict__ units, int n_units, int64_t n_items, int *cou
                     tc::fence_after_sync();
                     if (si + 1 < nb * G) {                     // B1 is free again
                         const int sn = si + 1;
-                        issue_b1(sn / G ? kB : kA, sn % G);
+                        issue_b1(min(k0 + bp + sn / G, nq - 1), sn % G);
                     }
                     if (pending2) {                            // B2 still read by MMA2
                         if (!wait_all(mbar2, ph2)) { aborted = true; break; }
@@ -498,26 +547,31 @@ TcShape tc_shape(const simus_plan *p, int T, int64_t S, double work_share, int i
     g.mh = g.Np > 128 ? 2 : 1;
     const size_t limit = 227 * 1024 - kHeader - 1024;
     const int tab_full = (p->delta_table && p->d_dtab) ? p->gc.tab_n : 0;
-    // Two tile buffers (geometry shared by bin pairs) with at most two transmit groups,
-    // else one buffer with the largest group that fits; the delta table where it still
-    // fits beside them; tensor memory holds D1 and QB * G * mh accumulator slices of nN
-    // columns.
-    for (int opt = 0; opt < 4 && !g.ok; ++opt) {
-        const int pair = (opt < 2 && p->pair_mode) ? 1 : 0;
-        const int tab_n = (opt & 1) ? 0 : tab_full;
-        for (int TG = std::min(T, 120); TG >= 1 && !g.ok; TG = (TG > 8 ? TG - 8 : TG - 1)) {
-            const int nN = ((2 * TG + 15) / 16) * 16;
-            const int G = (T + TG - 1) / TG;
-            if (pair && G > 2) break;
-            const int qb = (512 - nN) / (nN * G * g.mh);
-            if (qb < (pair ? 2 : 1)) continue;
-            const size_t sm = unit_smem(g.Np, nN, pair, p->M, tab_n);
-            if (sm > limit) continue;
-            g.ok = true;
-            g.TG = TG; g.nN = nN; g.pair = pair; g.n_groups = G; g.tab_n = tab_n;
-            g.QB = std::min(std::max(p->max_bins, pair ? 2 : 1), qb);
-            if (pair && (g.QB & 1)) g.QB -= 1;
-            g.smem = sm + kHeader;
+    // Three bins per generation pass (two tile buffers and a tensor-memory stash), else
+    // two (two buffers), else one, with at most two transmit groups when bins share a
+    // pass; the delta table where it still fits beside them; tensor memory holds D1,
+    // QB * G * mh accumulator slices of nN columns and the stash.
+    for (int mode = p->pair_mode; mode >= 0 && !g.ok; --mode) {
+        if (mode == 2 && g.mh != 1) continue;        // the stash holds one 128-column tile
+        const int per = mode + 1;                    // bins per generation pass
+        const int stash = mode == 2 ? g.Np : 0;      // tensor-memory columns of the stash
+        for (int tb = 0; tb < 2 && !g.ok; ++tb) {
+            const int tab_n = tb ? 0 : tab_full;
+            if (tb && !tab_full) break;
+            for (int TG = std::min(T, 120); TG >= 1 && !g.ok; TG = (TG > 8 ? TG - 8 : TG - 1)) {
+                const int nN = ((2 * TG + 15) / 16) * 16;
+                const int G = (T + TG - 1) / TG;
+                if (mode && G > 2) break;
+                const int qb = (512 - nN - stash) / (nN * G * g.mh);
+                if (qb < per) continue;
+                const size_t sm = unit_smem(g.Np, nN, mode ? 1 : 0, p->M, tab_n);
+                if (sm > limit) continue;
+                g.ok = true;
+                g.TG = TG; g.nN = nN; g.pair = mode; g.n_groups = G; g.tab_n = tab_n;
+                g.QB = std::min(std::max(p->max_bins, per), qb);
+                g.QB -= g.QB % per;
+                g.smem = sm + kHeader;
+            }
         }
     }
     if (!g.ok) return g;

@@ -471,12 +471,12 @@ int simus_plan_set_profiling(simus_plan *plan, int32_t enable) {
 
 int simus_plan_set_tuning(simus_plan *plan, const simus_tuning *t) {
     if (!plan || !t) return fail(SIMUS_ERR_ARG, "plan and tuning must not be NULL");
-    if (t->items_per_sm > 1024 || t->max_bins > 64 || t->chunks > 65536 || t->pair > 1 ||
+    if (t->items_per_sm > 1024 || t->max_bins > 64 || t->chunks > 65536 || t->pair > 2 ||
         t->delta_table > 1)
         return fail(SIMUS_ERR_ARG, "tuning value out of range");
     plan->items_per_sm = t->items_per_sm > 0 ? t->items_per_sm : 4;
     plan->max_bins = t->max_bins > 0 ? t->max_bins : 4;
-    plan->pair_mode = t->pair >= 0 ? t->pair : 1;
+    plan->pair_mode = t->pair >= 0 ? t->pair : 2;
     plan->delta_table = t->delta_table >= 0 ? t->delta_table : 1;
     plan->chunks = t->chunks > 0 ? t->chunks : 0;
     return SIMUS_OK;

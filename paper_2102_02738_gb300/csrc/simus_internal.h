@@ -65,7 +65,7 @@ struct simus_plan {
     bool stage_pending = false;
     int items_per_sm = 4;             // tensor-core path tuning (simus_tuning)
     int max_bins = 4;
-    int pair_mode = 1;
+    int pair_mode = 2;
     int delta_table = 1;
     int chunks = 0;
     bool profiling = false;
@@ -130,7 +130,8 @@ struct TcShape {
     int TG, n_groups;    // transmits per group, groups
     int nN;              // GEMM N of a group: 2 TG padded to 16
     int mh;              // receive GEMM M-halves: 1 (Np <= 128) or 2
-    int pair;            // 1: bins generated in pairs into two tile buffers
+    int pair;            // bins per generation pass - 1: 0 one tile buffer, 1 two,
+                         // 2 two buffers and a tensor-memory stash for the third bin
     int tab_n;           // delta-table intervals staged in shared memory (0: direct delta)
     int QB;              // bins per work item
     int n_btiles;

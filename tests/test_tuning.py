@@ -20,9 +20,10 @@ def test_candidates_cover_the_knobs():
     from paper_2102_02738_gb300 import autotune
     c = autotune.candidates(single=True)
     assert {k for d in c for k in d} == {"max_bins", "pair", "delta_table", "chunks"}
-    assert {d["pair"] for d in c} == {0, 1} and {d["delta_table"] for d in c} == {0, 1}
+    assert {d["pair"] for d in c} == {0, 1, 2} and {d["delta_table"] for d in c} == {0, 1}
     cb = autotune.candidates(single=False)
     assert {d["items_per_sm"] for d in cb} == {2, 4, 8}
+    assert {d["max_bins"] for d in c} == {2, 3, 4, 6}
     assert autotune._bucket(1) == 1 and autotune._bucket(1000) == 1024 and autotune._bucket(1024) == 1024
 
 
@@ -48,18 +49,22 @@ def rel_l2(a, b):
 def test_set_get_round_trip(S):
     w = ph.tiny(n_elements=16, n_scat=50, n_tx=3)
     plan = S.Plan(w.cfg, path="tc_f16")
-    assert plan.get_tuning() == dict(items_per_sm=4, max_bins=4, pair=1, delta_table=1, chunks=0)
+    assert plan.get_tuning() == dict(items_per_sm=4, max_bins=4, pair=2, delta_table=1, chunks=0)
     plan.set_tuning(max_bins=6, pair=0, delta_table=0, chunks=3, items_per_sm=8)
     assert plan.get_tuning() == dict(items_per_sm=8, max_bins=6, pair=0, delta_table=0, chunks=3)
     plan.set_tuning(max_bins=-1, pair=-1, delta_table=-1, chunks=0, items_per_sm=-1)
-    assert plan.get_tuning() == dict(items_per_sm=4, max_bins=4, pair=1, delta_table=1, chunks=0)
+    assert plan.get_tuning() == dict(items_per_sm=4, max_bins=4, pair=2, delta_table=1, chunks=0)
     with pytest.raises(S.SimusError):
         plan.set_tuning(max_bins=65)
+    with pytest.raises(S.SimusError):
+        plan.set_tuning(pair=3)
     plan.close()
 
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("tun", [dict(max_bins=2, pair=1, delta_table=1),
+                                 dict(max_bins=6, pair=2, delta_table=1),
+                                 dict(max_bins=3, pair=2, delta_table=0, chunks=3),
                                  dict(max_bins=6, pair=1, delta_table=0, chunks=2),
                                  dict(max_bins=3, pair=0, delta_table=1, chunks=1),
                                  dict(max_bins=8, pair=0, delta_table=0)])
