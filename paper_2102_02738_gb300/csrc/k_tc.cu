@@ -13,7 +13,8 @@
 //   reflection + receive sum (Eq. 30-32)   RF_q[e][t] += sum_s G[s][e] R_s P[s][t]
 //       A^T read from the same tile as an MN-major operand: M = e (in halves of 128 when
 //       Np > 128), K = (s | s) over the Re G and Im G halves -- no transposed copy
-//       B2 rows 2t   = [ Re P' | -Im P' ],  rows 2t+1 = [ Im P' | Re P' ],  P' = R_s P
+//       B2 rows 2t   = [ Re P' | -Im P' ],  rows 2t+1 = [ Im P' | Re P' ],  P' = R_s P,
+//       stored MN-major so that one thread's transmits are contiguous
 //       D2[bin][half] columns (2t, 2t+1) = (Re RF, Im RF), accumulated over every
 //       scatterer tile of the work item in tensor memory.
 //
@@ -341,7 +342,7 @@ k_tc_rf(const TcUnit *__restrict__ units, int n_units, int64_t n_items, int *cou
         const uint32_t abuf0 = tc::smem_u32(A0), abuf1 = tc::smem_u32(A1);
         const uint32_t b1s = tc::smem_u32(B1), b2s = tc::smem_u32(B2);
         const uint32_t idesc1 = tc::idesc_f16(128, nN, BF16);
-        const uint32_t idesc2 = idesc1 | (1u << 15);          // A operand MN-major
+        const uint32_t idesc2 = idesc1 | (1u << 15) | (1u << 16);   // A and B MN-major
         const uint32_t b1_bytes = (uint32_t)nN * K1 * 2;
         if (ui != cur_unit) {
             for (int i = tid; i < M; i += kThreads) sub[i] = U.sub[i];
@@ -443,7 +444,10 @@ k_tc_rf(const TcUnit *__restrict__ units, int n_units, int64_t n_items, int *cou
                         ph2 ^= 1;
                         pending2 = false;
                     }
-                    // ---- P' = R_s P -> B2
+                    // ---- P' = R_s P -> B2, MN-major (the 8 transmit rows of a core matrix
+                    // are contiguous for one scatterer): row 2t = (Re P' | -Im P'), row
+                    // 2t+1 = (Im P' | Re P') over K = (s | 128 + s), four 16-byte stores
+                    // per thread and 8 transmits
                     {
                         const int sp = warp & 3, cc = warp >> 2;
                         const int s = sp * 32 + lane;
@@ -451,17 +455,22 @@ k_tc_rf(const TcUnit *__restrict__ units, int n_units, int64_t n_items, int *cou
                         for (int c0 = cc * 16; c0 < nN; c0 += 64) {
                             float v[16];
                             tc::tmem_ld16(tmem + ((uint32_t)(sp * 32) << 16) + (uint32_t)c0, v);
+                            uint32_t w0[8], w1[8];
 #pragma unroll
                             for (int i = 0; i < 8; ++i) {
                                 const int t = (c0 >> 1) + i;
                                 float pr = 0.f, pi = 0.f;
                                 if (t < TGg) { pr = R * v[2 * i]; pi = R * v[2 * i + 1]; }
-                                const int n0 = 2 * t;
-                                *reinterpret_cast<uint16_t *>(B2 + tc::kmajor_offset(n0, s, 256)) = h16<BF16>(pr);
-                                *reinterpret_cast<uint16_t *>(B2 + tc::kmajor_offset(n0, 128 + s, 256)) = h16<BF16>(-pi);
-                                *reinterpret_cast<uint16_t *>(B2 + tc::kmajor_offset(n0 + 1, s, 256)) = h16<BF16>(pi);
-                                *reinterpret_cast<uint16_t *>(B2 + tc::kmajor_offset(n0 + 1, 128 + s, 256)) = h16<BF16>(pr);
+                                w0[i] = h16x2<BF16>(pr, pi);
+                                w1[i] = h16x2<BF16>(-pi, pr);
                             }
+                            const uint32_t nrow = (uint32_t)(nN >> 3);
+                            unsigned char *q0 = B2 + ((((uint32_t)(s >> 3) * nrow + (uint32_t)(c0 >> 3)) << 7) + ((s & 7) << 4));
+                            unsigned char *q1 = q0 + ((16u * nrow) << 7);        // k = 128 + s
+                            *reinterpret_cast<uint4 *>(q0) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+                            *reinterpret_cast<uint4 *>(q0 + 128) = make_uint4(w0[4], w0[5], w0[6], w0[7]);
+                            *reinterpret_cast<uint4 *>(q1) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+                            *reinterpret_cast<uint4 *>(q1 + 128) = make_uint4(w1[4], w1[5], w1[6], w1[7]);
                         }
                     }
                     tc::fence_proxy_async_smem();
@@ -481,7 +490,7 @@ k_tc_rf(const TcUnit *__restrict__ units, int n_units, int64_t n_items, int *cou
                                 const uint32_t a0 = abase + (uint32_t)((2 * (j & 7)) * 16 * K1)
                                                   + (uint32_t)((j >> 3) * (Np / 8) * 128) + (uint32_t)(h * 16 * 128);
                                 uint64_t ad = tc::smem_desc(a0, 16 * K1, 128);
-                                uint64_t bd = tc::smem_desc(b2s + 256 * j, 128, 4096);
+                                uint64_t bd = tc::smem_desc(b2s + (uint32_t)(32 * nN * j), 16 * nN, 128);
                                 tc::mma_f16(d2, ad, bd, idesc2, (j > 0 || tile > tile0) ? 1u : 0u);
                             }
                         }

@@ -351,7 +351,8 @@ void plan_fill_tables(const simus_plan *p, SubElem *sub, float2 *H) {
             s.zl = (float)(zc - (double)s.zh);
             s.cpsi = (float)std::cos(psi);
             s.spsi = (float)std::sin(psi);
-            s.pad0 = s.pad1 = 0.f;
+            s.l0 = (float)(xc * std::cos(psi) - zc * std::sin(psi));
+            s.z0 = (float)(xc * std::sin(psi) + zc * std::cos(psi));
         }
 }
 

@@ -41,7 +41,8 @@ struct GreenConst {
 struct __align__(16) SubElem {
     float xh, xl, zh, zl;   // x_c = xh + xl, z_c = zh + zl
     float cpsi, spsi;       // normal (sin psi, cos psi); local frame rotation
-    float pad0, pad1;
+    float l0, z0;           // the centroid rotated into that frame (x_c cpsi - z_c spsi,
+                            // x_c spsi + z_c cpsi), for the FP32 setup of the TC path
 };
 
 }  // namespace simus
