@@ -38,7 +38,7 @@ def build(force: bool = False) -> str:
 class Params(C.Structure):
     _fields_ = [
         ("n_elements", C.c_int32), ("n_sub", C.c_int32), ("baffle", C.c_int32),
-        ("pulse", C.c_int32), ("n_samples", C.c_int32), ("pad_", C.c_int32),
+        ("pulse", C.c_int32), ("n_samples", C.c_int32), ("two_d", C.c_int32),
         ("pitch", C.c_double), ("width", C.c_double), ("height", C.c_double),
         ("elev_focus", C.c_double), ("radius", C.c_double), ("fc", C.c_double),
         ("frac_bw", C.c_double), ("zeta", C.c_double), ("c", C.c_double),
@@ -90,7 +90,7 @@ def lib():
 
 def params(cfg: dict) -> Params:
     p = Params()
-    for name in ("n_elements", "n_sub", "baffle", "pulse", "n_samples"):
+    for name in ("n_elements", "n_sub", "baffle", "pulse", "n_samples", "two_d"):
         setattr(p, name, int(cfg.get(name, 0)))
     for name in ("pitch", "width", "height", "elev_focus", "radius", "fc", "frac_bw",
                  "zeta", "c", "alpha_db", "fs", "pulse_cycles"):

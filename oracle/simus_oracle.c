@@ -35,6 +35,9 @@
  *       evaluated with that r_n.
  *   R11 Hann pulse: window 0.5(1+cos(2 pi t/T)) on [-T/2,T/2] applied to the sine of
  *       Eq. 25, i.e. S_P^Hann(w) = S_P(w)/2 + S_P(w+2pi/T)/4 + S_P(w-2pi/T)/4.
+ *   R14 2-D mode (Section V, Eq. 36-38): the Green's term is exp(i(k + i k_a) r)/sqrt(r)
+ *       * D(theta, k), with the constants sqrt(2b), 2b and the sqrt(k) inside P_Tx dropped
+ *       as in R3 (P_Tx stays S_P sqrt(S_T)); h and R_f play no part and Y must be 0.
  *
  * Gradients (oracle_rf_grad) are not in the paper; they are the exact derivative of
  * the model above and are pinned by central finite differences of oracle_rf.
@@ -54,7 +57,7 @@ typedef struct {
     int32_t baffle;       /* 0 soft, 1 rigid, 2 finite impedance (Eq. 39) */
     int32_t pulse;        /* 0 rectangular window (Eq. 25), 1 Hann window (R11) */
     int32_t n_samples;    /* Nt, RF samples per channel */
-    int32_t pad_;
+    int32_t two_d;        /* 1: the 2-D model of Section V (R14), 0: 3-D */
     double pitch;         /* p [m] */
     double width;         /* 2b [m] */
     double height;        /* h [m] */
@@ -249,7 +252,8 @@ static double absorption(const oracle_params *p, double k)
 }
 
 /* Eq. 17/19 with Eq. 39 and Eq. 40: the Green's term of sub-element n at frequency f,
- *   g = exp(i (k + i k_a) r) / r * D(theta, k) * delta(Y, r, k). */
+ *   g = exp(i (k + i k_a) r) / r * D(theta, k) * delta(Y, r, k);
+ * in 2-D (Eq. 36, R14) g = exp(i (k + i k_a) r) / sqrt(r) * D(theta, k). */
 static cplx green(const oracle_params *p, int32_t nu, double f, double xc, double zc,
                   double psi, double X, double Y, double Z)
 {
@@ -258,6 +262,7 @@ static cplx green(const oracle_params *p, int32_t nu, double f, double xc, doubl
     geom G = geometry(xc, zc, psi, X, Y, Z);
     double D = oracle_directivity(p, k, p->width / 2.0 / nu, G.sin_t, G.cos_t);
     if (D == 0.0) return 0.0;
+    if (p->two_d) return cexp(I * (k + I * ka) * G.r) / sqrt(G.r) * D;
     return cexp(I * (k + I * ka) * G.r) / G.r * D * oracle_delta_c(p, k, Y, G.r);
 }
 
@@ -451,9 +456,15 @@ static void green_grad(const oracle_params *p, int32_t nu, double f, double xc, 
     geom G = geometry(xc, zc, psi, X, Y, Z);
     if (G.cos_t <= 0.0) { *g = *gx = *gz = 0.0; return; }
 
-    /* E(r) = exp(i (k + i ka) r) / r and dE/dr */
-    cplx E = cexp(I * (k + I * ka) * G.r) / G.r;
-    cplx dE = E * (I * k - ka - 1.0 / G.r);
+    /* E(r) = exp(i (k + i ka) r) / r and dE/dr; 2-D: / sqrt(r), no delta (R14) */
+    cplx E, dE;
+    if (p->two_d) {
+        E = cexp(I * (k + I * ka) * G.r) / sqrt(G.r);
+        dE = E * (I * k - ka - 0.5 / G.r);
+    } else {
+        E = cexp(I * (k + I * ka) * G.r) / G.r;
+        dE = E * (I * k - ka - 1.0 / G.r);
+    }
 
     /* delta(r) and d delta / dr (Eq. 14-16 differentiated in r) */
     double h = p->height;
@@ -462,7 +473,8 @@ static void green_grad(const oracle_params *p, int32_t nu, double f, double xc, 
     cplx beta = -I * k * Y / r, dbeta = I * k * Y / (r * r);
     cplx gamma = I * k * Y * Y / (2.0 * r), dgamma = -I * k * Y * Y / (2.0 * r * r);
     cplx delta = 0.0, ddelta = 0.0;
-    for (int gg = 0; gg < 4; ++gg) {
+    if (p->two_d) delta = 1.0;
+    for (int gg = 0; gg < 4 && !p->two_d; ++gg) {
         cplx A = A_RE[gg] + I * A_IM[gg];
         cplx B = B_RE[gg] + I * B_IM[gg];
         cplx alpha = B / (h * h) + I * k / 2.0 * (inv_rf - 1.0 / r);

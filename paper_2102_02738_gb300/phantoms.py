@@ -260,14 +260,17 @@ def ragged_batch(seed=1005, n_sims=256, s_min=1000, s_max=1_000_000, scale=1.0):
 
 
 def tiny(seed=7, n_elements=4, n_scat=5, n_tx=2, n_sub=2, fc=5e6, nt=None, convex=False,
-         baffle=0, pulse=0, y_spread=0.0, alpha_db=0.5, height=5e-3, elev_focus=18e-3):
-    """Small problems for exhaustive checks."""
+         baffle=0, pulse=0, y_spread=0.0, alpha_db=0.5, height=5e-3, elev_focus=18e-3,
+         two_d=False):
+    """Small problems for exhaustive checks (two_d: the 2-D model of Section V)."""
     if convex:
         probe = convex_probe(n_elements, fc, 0.5e-3, 0.05e-3, 20e-3, height=height,
                              elev_focus=elev_focus, n_sub=n_sub, baffle=baffle)
     else:
         probe = linear_probe(n_elements, fc, 0.3e-3, 0.03e-3, height=height,
                              elev_focus=elev_focus, n_sub=n_sub, baffle=baffle)
+    if two_d:
+        probe["two_d"] = 1
     med = medium(fc, pulse=pulse, alpha_db=alpha_db)
     x, z, rc = _box(seed, n_scat, -3e-3, 3e-3, 4e-3, 12e-3)
     y = None if y_spread == 0 else y_spread * (2 * uniform(seed, 5, n_scat) - 1)

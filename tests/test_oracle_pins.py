@@ -270,6 +270,76 @@ def test_subelement_sum_converges_to_aperture_integral(oracle, baffle):
         errs.append(e_nu)
 
 
+# ------------------------------------------------------------ Section V: the 2-D case
+def test_two_d_green_is_the_three_d_limit(oracle):
+    """Eq. 35-36: with h, R_f -> inf the 3-D term e^{ikr}/r D delta tends to
+    0.95 sqrt(2 i pi / k) e^{ikr}/sqrt(r) D, i.e. (sum A_g) sqrt(2 i pi / k) times the
+    2-D term (the 3-D delta itself is pinned by quadrature above)."""
+    base = ph.tiny(n_elements=3, n_sub=2, height=1e4, elev_focus=math.inf).cfg
+    c2 = dict(base, two_d=1)
+    for f, X, Z, n in ((3e6, 0.4e-3, 7e-3, 0), (6e6, -1.5e-3, 11e-3, 3), (4.5e6, 2e-3, 5e-3, 5)):
+        k = 2 * math.pi * f / base["c"]
+        g3 = oracle.green(base, f, X, 0.0, Z, n)
+        g2 = oracle.green(c2, f, X, 0.0, Z, n)
+        assert abs(g2) > 0
+        assert g3 == pytest.approx(0.95 * np.sqrt(2j * math.pi / k) * g2, rel=1e-6)
+
+
+def test_two_d_is_independent_of_height_and_focus(oracle):
+    a = ph.tiny(two_d=True, height=5e-3, elev_focus=18e-3).cfg
+    b = dict(a, height=1e-2, elev_focus=math.inf)
+    for f, X, Z, n in ((5e6, 0.3e-3, 6e-3, 1), (7e6, -0.9e-3, 10e-3, 2)):
+        assert oracle.green(a, f, X, 0.0, Z, n) == oracle.green(b, f, X, 0.0, Z, n)
+
+
+@pytest.mark.parametrize("baffle", [0, 1])
+def test_two_d_subelement_sum_converges_to_line_aperture_integral(oracle, baffle):
+    """Eq. 37 with one element: the nu far-field sub-elements (width 2b/nu each)
+    converge to the integral of e^{ikr'}/sqrt(r') (obliquity) over the aperture."""
+    f, c = 5e6, 1540.0
+    lam = c / f
+    k = 2 * math.pi / lam
+    b = lam
+    cfg_base = dict(ph.linear_probe(1, f, 2 * lam, 0.0, baffle=baffle), **ph.medium(f, alpha_db=0.0),
+                    n_samples=100, two_d=1)
+    for X, Z in ((0.0, 5 * lam), (2.5 * lam, 4 * lam), (-1.0 * lam, 6 * lam)):
+        def integrand(xp):
+            r = math.hypot(X - xp, Z)
+            ob = Z / r if baffle == 0 else 1.0
+            return np.exp(1j * k * r) / math.sqrt(r) * ob
+
+        exact = quad_c(integrand, -b, b)
+        e_nu = []
+        for nu in (1, 2, 4, 8, 16, 32):
+            cfg = dict(cfg_base, n_sub=nu)
+            s = sum(oracle.green(cfg, f, X, 0.0, Z, n) for n in range(nu)) * (2 * b / nu)
+            e_nu.append(abs(s - exact) / abs(exact))
+        assert all(e_nu[i + 1] < e_nu[i] for i in range(len(e_nu) - 1)), e_nu
+        assert e_nu[-1] < 2e-3
+
+
+def test_two_d_two_way_arrival_time(oracle):
+    """2-D (Eq. 38): one element transmits, one scatterer; the echo envelope on element m
+    peaks at (r_tx + r_rx)/c."""
+    w = ph.tiny(n_elements=4, n_sub=1, n_tx=1, alpha_db=0.0, nt=1200, two_d=True)
+    cfg = w.cfg
+    delays = np.zeros((1, 4))
+    apod = np.zeros((1, 4))
+    apod[0, 2] = 1.0
+    X, Z = np.array([-0.4e-3]), np.array([8e-3])
+    lo, hi, n = oracle.bins(cfg)
+    q = np.arange(lo, hi + 1)
+    Xq = oracle.rf_spectrum(cfg, delays, apod, X, None, Z, [1.0], q)[0]
+    xc, _, _ = oracle.centroids(cfg)
+    c, fs, nt = cfg["c"], cfg["fs"], cfg["n_samples"]
+    wq = 2 * np.pi * q * fs / nt
+    for m in range(4):
+        tau = (math.hypot(X[0] - xc[2], Z[0]) + math.hypot(X[0] - xc[m], Z[0])) / c
+        t = tau + np.linspace(-2, 2, 4001) / fs
+        env = np.abs(np.exp(-1j * np.outer(t, wq)) @ Xq[m])
+        assert abs(t[np.argmax(env)] - tau) * fs < 2e-3
+
+
 # ------------------------------------------------------------------- arrival time
 @pytest.mark.parametrize("delay_us", [0.0, 2.0])
 def test_two_way_arrival_time(oracle, delay_us):
@@ -387,9 +457,10 @@ def test_pfield_midpoint_sum_approximates_integral(oracle):
 
 
 # -------------------------------------------------------------------- gradients (FD)
-@pytest.mark.parametrize("convex,y", [(False, 0.0), (True, 0.0), (False, 0.7e-3)])
-def test_green_grad_finite_differences(oracle, convex, y):
-    cfg = ph.tiny(convex=convex, n_sub=2).cfg
+@pytest.mark.parametrize("convex,y,two_d", [(False, 0.0, False), (True, 0.0, False),
+                                            (False, 0.7e-3, False), (True, 0.0, True)])
+def test_green_grad_finite_differences(oracle, convex, y, two_d):
+    cfg = ph.tiny(convex=convex, n_sub=2, two_d=two_d).cfg
     h = 1e-8
     for (X, Z, n, f) in ((0.5e-3, 6e-3, 1, 4e6), (-1.2e-3, 9e-3, 3, 6.5e6)):
         g, gx, gz = oracle.green_grad(cfg, f, X, y, Z, n)
@@ -400,8 +471,9 @@ def test_green_grad_finite_differences(oracle, convex, y):
         assert gz == pytest.approx(fz, rel=2e-6)
 
 
-def test_rf_grad_finite_differences(oracle):
-    w = ph.tiny(n_elements=4, n_sub=2, n_scat=4, n_tx=2, nt=256)
+@pytest.mark.parametrize("two_d", [False, True])
+def test_rf_grad_finite_differences(oracle, two_d):
+    w = ph.tiny(n_elements=4, n_sub=2, n_scat=4, n_tx=2, nt=256, two_d=two_d)
     cfg = w.cfg
     x, z, R = (w.x.astype(np.float64), w.z.astype(np.float64), w.rc.astype(np.float64))
     d, a = w.delays.astype(np.float64), w.apod.astype(np.float64)
