@@ -71,10 +71,13 @@ typedef struct simus_probe {
     int32_t n_sub;      /* nu sub-elements per element; 0 = Eq. 21 with lambda_min at
                            the upper -6 dB edge c / (fc (1 + frac_bw / 2))             */
     int32_t baffle;     /* SIMUS_BAFFLE_*                                            */
-    int32_t reserved;   /* must be 0                                                 */
+    int32_t two_d;      /* 0: 3-D model (Eq. 17, elevation factor delta of Eq. 16);
+                           1: the 2-D x-z model of Section V (Eq. 36-38): Green's term
+                           exp(i(k + i k_a) r)/sqrt(r) D(theta, k), height and
+                           elev_focus unused, scatterer and field-point y must be NULL */
     double pitch;       /* p [m] > 0                                                 */
     double width;       /* element width 2b [m], 0 < width <= pitch                   */
-    double height;      /* element height h [m] > 0                                   */
+    double height;      /* element height h [m] > 0 (3-D)                              */
     double elev_focus;  /* elevation focus R_f [m] > 0; +INFINITY = no lens           */
     double radius;      /* convex radius of curvature [m]; 0 = linear array           */
     double fc;          /* centre frequency [Hz] > 0                                  */

@@ -139,7 +139,8 @@ k_grad(const GreenConst gc, const SubElem *__restrict__ sub_g, const float *__re
 #pragma unroll
                 for (int j = 0; j < QB; ++j) {
                     const float q = q0 + (float)j;
-                    const float amp = gc.h * P.inv_r * ex2_a(-q * gc.att2 * P.rh);
+                    const float amp = (gc.two_d ? rsqrt_a(P.rh) : gc.h * P.inv_r) *
+                                      ex2_a(-q * gc.att2 * P.rh);
                     float2 g, gx, gz;
                     green_grad_term<NARROW>(gc, P, Q, q, amp, g, gx, gz);
                     G[j].x += g.x; G[j].y += g.y;

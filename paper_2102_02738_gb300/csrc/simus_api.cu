@@ -48,8 +48,9 @@ int validate_probe(const simus_probe *pr, const simus_medium *md) {
     if (pr->n_sub < 0 || pr->n_sub > 64) return fail(SIMUS_ERR_ARG, "n_sub=%d outside [0, 64]", pr->n_sub);
     if (!(pr->pitch > 0) || !(pr->width > 0) || pr->width > pr->pitch * (1 + 1e-12))
         return fail(SIMUS_ERR_ARG, "need 0 < width <= pitch (width=%g pitch=%g)", pr->width, pr->pitch);
-    if (!(pr->height > 0)) return fail(SIMUS_ERR_ARG, "height must be > 0");
-    if (!(pr->elev_focus > 0)) return fail(SIMUS_ERR_ARG, "elev_focus must be > 0 or +inf");
+    if (pr->two_d != 0 && pr->two_d != 1) return fail(SIMUS_ERR_ARG, "two_d must be 0 or 1");
+    if (!pr->two_d && !(pr->height > 0)) return fail(SIMUS_ERR_ARG, "height must be > 0");
+    if (!pr->two_d && !(pr->elev_focus > 0)) return fail(SIMUS_ERR_ARG, "elev_focus must be > 0 or +inf");
     if (!(pr->radius >= 0) || std::isinf(pr->radius)) return fail(SIMUS_ERR_ARG, "radius must be finite and >= 0");
     if (!(pr->fc > 0) || std::isinf(pr->fc)) return fail(SIMUS_ERR_ARG, "fc must be > 0");
     if (!(pr->frac_bw > 0) || !(pr->frac_bw < 2)) return fail(SIMUS_ERR_ARG, "frac_bw must be in (0, 2)");
@@ -112,8 +113,9 @@ int validate_tx(const simus_plan *p, const simus_tx *tx) {
     return SIMUS_OK;
 }
 
-int validate_scat(const simus_scat *sc) {
+int validate_scat(const simus_scat *sc, int two_d) {
     if (!sc) return fail(SIMUS_ERR_ARG, "scat must not be NULL");
+    if (two_d && sc->y) return fail(SIMUS_ERR_ARG, "scat.y must be NULL for a 2-D probe (x-z model)");
     if (sc->n < 0 || sc->n > (int64_t)1 << 34) return fail(SIMUS_ERR_ARG, "scat.n=%lld out of range", (long long)sc->n);
     if (sc->n == 0) return SIMUS_OK;
     int rc;
@@ -250,8 +252,10 @@ GreenConst green_const(const simus_probe &pr, const simus_medium &md, int N, int
     // Eq. 40: k_a = alpha_dB / 8.69 * f * 1e-4 per metre; base 2 per bin.
     gc.att2 = (float)(medium->alpha_db / 8.69 * df * 1e-4 / std::log(2.0));
     gc.zeta = (float)probe->zeta;
-    gc.h = (float)probe->height;
-    gc.h2 = (float)(probe->height * probe->height);
+    gc.two_d = probe->two_d;
+    gc.h = probe->two_d ? 1.0f : (float)probe->height;          // 2-D: no delta (Section V)
+    gc.h2 = probe->two_d ? 0.0f : (float)(probe->height * probe->height);
+    if (probe->two_d) gc.inv_rf = 0.0f;
     gc.narrow = (2.0 * M_PI * K * b / nu) * q_max <= 3.19 ? 1 : 0;
     gc.df = df;
     return gc;
@@ -264,6 +268,7 @@ void plan_delta_table(simus_plan *p, std::vector<float4> &tab) {
     GreenConst &gc = p->gc;
     gc.tab_n = 0;
     tab.clear();
+    if (p->probe.two_d) return;   // no elevation factor in 2-D
     const double kx = M_PI * gc.df / p->medium.c * p->probe.height * p->probe.height;  // x per bin per (1/m)
     const double inv_rf = std::isinf(p->probe.elev_focus) ? 0.0 : 1.0 / p->probe.elev_focus;
     const double inv_r_max = 1.0 / 2e-3;
@@ -737,7 +742,7 @@ int simus_rf_spectrum(simus_plan *plan, const simus_tx *tx, const simus_scat *sc
     int rc;
     if ((rc = use_plan_device(plan))) return rc;
     if ((rc = validate_tx(plan, tx))) return rc;
-    if ((rc = validate_scat(scat))) return rc;
+    if ((rc = validate_scat(scat, plan->probe.two_d))) return rc;
     if ((rc = check_device_ptr(spec, "spec"))) return rc;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (scat->n == 0)
@@ -756,7 +761,7 @@ int simus_rf(simus_plan *plan, const simus_tx *tx, const simus_scat *scat, float
     int rc;
     if ((rc = use_plan_device(plan))) return rc;
     if ((rc = validate_tx(plan, tx))) return rc;
-    if ((rc = validate_scat(scat))) return rc;
+    if ((rc = validate_scat(scat, plan->probe.two_d))) return rc;
     if ((rc = check_device_ptr(rf, "rf"))) return rc;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const int n_chan = tx->n_tx * plan->N;
@@ -781,6 +786,7 @@ int simus_pfield(simus_plan *plan, const simus_tx *tx, int64_t n_pts, const floa
     if ((rc = check_device_ptr(x, "x")) || (rc = check_device_ptr(y, "y", true)) ||
         (rc = check_device_ptr(z, "z")) || (rc = check_device_ptr(prms, "prms")))
         return rc;
+    if (plan->probe.two_d && y) return fail(SIMUS_ERR_ARG, "y must be NULL for a 2-D probe (x-z model)");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const double df = 2.0 * plan->probe.fc / n_freq;            // midpoint grid of Eq. 42 (R8)
     const double dw = 2.0 * M_PI * df;
@@ -824,7 +830,7 @@ int simus_rf_grad(simus_plan *plan, const simus_tx *tx, const simus_scat *scat, 
     int rc;
     if ((rc = use_plan_device(plan))) return rc;
     if ((rc = validate_tx(plan, tx))) return rc;
-    if ((rc = validate_scat(scat))) return rc;
+    if ((rc = validate_scat(scat, plan->probe.two_d))) return rc;
     if (scat->y) return fail(SIMUS_ERR_ARG, "simus_rf_grad needs scatterers in the azimuth plane (y == NULL)");
     if ((rc = check_device_ptr(drf, "drf"))) return rc;
     if ((rc = check_device_ptr(g_rc, "g_rc", true)) || (rc = check_device_ptr(g_x, "g_x", true)) ||
@@ -881,7 +887,7 @@ int simus_batch_rf(int32_t n_sims, simus_plan *const *plans, const simus_tx *tx,
     }
     if ((rc = use_plan_device(plans[0]))) return rc;
     for (int i = 0; i < n_sims; ++i) {
-        if ((rc = validate_tx(plans[i], &tx[i])) || (rc = validate_scat(&scat[i])) ||
+        if ((rc = validate_tx(plans[i], &tx[i])) || (rc = validate_scat(&scat[i], plans[i]->probe.two_d)) ||
             (rc = check_device_ptr(rf[i], "rf[i]")))
             return fail(rc, "simulation %d: %s", i, simus_last_error());
     }
@@ -961,7 +967,7 @@ extern "C" int simus_rf_noalloc(const simus_probe *probe, const simus_medium *me
         return fail(SIMUS_ERR_ARG, "simus_rf_noalloc serves nu*N <= %d and <= %d kept bins (got %d, %d)",
                     kNoallocMaxSub, kNoallocMaxBins, plan.M, plan.nq);
     if ((rc = validate_tx(&plan, tx))) return rc;
-    if ((rc = validate_scat(scat))) return rc;
+    if ((rc = validate_scat(scat, plan.probe.two_d))) return rc;
     if ((rc = check_device_ptr(rf, "rf"))) return rc;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const int T = tx->n_tx, n_chan = T * plan.N;

@@ -20,7 +20,7 @@ struct GreenConst {
     int32_t nq;       // number of kept bins
     int32_t nt;       // RF samples
     int32_t baffle;   // SIMUS_BAFFLE_*
-    int32_t pad_;
+    int32_t two_d;    // 1: 2-D model (Section V): amplitude 1/sqrt(r), delta = 1
     float Kh, Kl;     // df / c as a double-float [cycles per metre per bin]
     float k1;         // 2 pi df / c [rad per metre per bin]
     float k1b;        // k1 * b / nu: sinc argument per bin per unit sin(theta)

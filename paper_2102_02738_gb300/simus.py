@@ -34,7 +34,7 @@ class SimusError(RuntimeError):
 
 class Probe(C.Structure):
     _fields_ = [("n_elements", C.c_int32), ("n_sub", C.c_int32), ("baffle", C.c_int32),
-                ("reserved", C.c_int32), ("pitch", C.c_double), ("width", C.c_double),
+                ("two_d", C.c_int32), ("pitch", C.c_double), ("width", C.c_double),
                 ("height", C.c_double), ("elev_focus", C.c_double), ("radius", C.c_double),
                 ("fc", C.c_double), ("frac_bw", C.c_double), ("zeta", C.c_double)]
 
@@ -119,7 +119,8 @@ def _check(rc):
 # ------------------------------------------------------------------- marshalling
 def probe_struct(cfg: dict) -> Probe:
     ef = cfg.get("elev_focus", math.inf)
-    return Probe(int(cfg["n_elements"]), int(cfg.get("n_sub", 0)), int(cfg.get("baffle", 0)), 0,
+    return Probe(int(cfg["n_elements"]), int(cfg.get("n_sub", 0)), int(cfg.get("baffle", 0)),
+                 int(cfg.get("two_d", 0)),
                  float(cfg["pitch"]), float(cfg["width"]), float(cfg["height"]),
                  float(ef if ef is not None else math.inf), float(cfg.get("radius", 0.0)),
                  float(cfg["fc"]), float(cfg["frac_bw"]), float(cfg.get("zeta", 1.75)))
