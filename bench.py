@@ -30,6 +30,10 @@ sys.path.insert(0, ROOT)
 
 from paper_2102_02738_gb300 import phantoms as ph  # noqa: E402
 
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch of the dominant kernel, from
+# the ncu capture summarised in profiles/ (per launch; absent where the kernel changed
+# after the capture or none was taken)
+NCU_TRAFFIC = {("diverging-convex-128", "tc_f16", 100000): 53.171968e6 + 225.137408e6}
 METRIC = "Green's terms/s (freq x scatterer x sub-elem x tx)"
 WORKLOADS = {
     "planewave-linear-128": ph.planewave_linear_128,
@@ -342,7 +346,8 @@ def run_ours(args, rank, ws, local):
                    "parallelism": "replicas" if ws > 1 else "single-gpu"},
         "roofline": {"bound": "alu", "kernel": "green+contraction",
                      "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gterm/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     "traffic": NCU_TRAFFIC.get((args.workload, path, w.n_scat)),
                      "peak_source": f"{peak_src}: min(SMs*128*clk/{FP32_PER_TERM}, "
                                     f"SMs*16*clk/{MUFU_PER_TERM}), {n_sm} SMs at "
                                     f"{peaks.get('sm_max_mhz', 2070.0)} MHz",
