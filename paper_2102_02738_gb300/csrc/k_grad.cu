@@ -290,7 +290,7 @@ int launch_adjoint_dft(const simus_plan *p, const float *drf, int T, float2 *lam
 
 int launch_grad(const simus_plan *p, const GradGeom &g, const simus_scat *sc, int T,
                 const float2 *cw, const float2 *lam, float *gpart, float2 *bpart, cudaStream_t st) {
-    auto kern = p->gc.narrow ? k_grad<true> : k_grad<false>;
+    auto kern = p->gc.narrow == 1 ? k_grad<true> : k_grad<false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
     if (e != cudaSuccess) return check_cuda(e, "k_grad smem attribute");
     dim3 grid(g.n_qtiles, g.n_chunks);

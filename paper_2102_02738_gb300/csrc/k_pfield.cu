@@ -110,7 +110,7 @@ int launch_pfield(const simus_plan *p, const GreenConst &gc, const simus_tx *tx,
         if (rc) return rc;
     }
     const size_t smem = sizeof(SubElem) * p->M + sizeof(float2) * (size_t)kPQB * p->N;
-    const bool has_y = y != nullptr, narrow = gc.narrow != 0;
+    const bool has_y = y != nullptr, narrow = gc.narrow == 1;
     auto kern = has_y ? (narrow ? k_pfield<true, true> : k_pfield<true, false>)
                       : (narrow ? k_pfield<false, true> : k_pfield<false, false>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -192,7 +192,7 @@ PlainGeom plain_geometry(const simus_plan *p, int T, int64_t S) {
 int launch_plain(const simus_plan *p, const PlainGeom &g, const simus_scat *sc, int T,
                  const float2 *cw, float2 *part, cudaStream_t st) {
     dim3 grid(g.n_qtiles, g.n_chunks, T);
-    const bool has_y = sc->y != nullptr, narrow = p->gc.narrow != 0;
+    const bool has_y = sc->y != nullptr, narrow = p->gc.narrow == 1;
     auto kern = has_y ? (narrow ? k_plain_rf<kPlainQB, true, true> : k_plain_rf<kPlainQB, true, false>)
                       : (narrow ? k_plain_rf<kPlainQB, false, true> : k_plain_rf<kPlainQB, false, false>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,

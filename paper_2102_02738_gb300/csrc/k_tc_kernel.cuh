@@ -1,0 +1,530 @@
+// k_tc_kernel.cuh -- the persistent tensor-core kernel k_tc_rf and its device helpers.
+// Included by the translation units that instantiate it (k_tc_rf_*.cu, one per group of
+// template arguments, compiled in parallel) and by k_tc.cu for the shared constants.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "green.cuh"
+#include "simus_internal.h"
+#include "tcgen05.cuh"
+
+namespace simus {
+
+namespace {
+constexpr int kThreads = 512;
+constexpr int kSB = 128;          // scatterers per tile
+constexpr int kMaxWait = 1 << 22; // polls before a wait is declared timed out
+constexpr size_t kHeader = 128;   // mbarriers, tensor-memory slot, flags, item index
+
+// FP16 or BF16 (bf16 is uniform over a launch) pair of halves, lo in the low 16 bits
+__device__ __forceinline__ uint32_t h16x2(bool bf16, float lo, float hi) {
+    if (bf16) {
+        const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+        return *reinterpret_cast<const uint32_t *>(&v);
+    }
+    const __half2 v = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&v);
+}
+
+// delta / h from the table of cubic pieces: interval i holds c0..c3 (complex) of
+// c0 + c1 u + c2 u^2 + c3 u^3, u = t - i, t = (x - x0) / dx (two float4 per interval).
+__device__ __forceinline__ float2 cubic_piece(const float4 &lo, const float4 &hi, float u) {
+    return make_float2(fmaf(u, fmaf(u, fmaf(u, hi.z, hi.x), lo.z), lo.x),
+                       fmaf(u, fmaf(u, fmaf(u, hi.w, hi.y), lo.w), lo.y));
+}
+
+// Sub-element sums (Eq. 33) of the Green's terms of elements e0 and e0 + 1 for one
+// scatterer at the NB consecutive bins qA, qA + 1, ...: two independent evaluation chains
+// side by side, so that each warp has twice the instruction-level parallelism, and one
+// geometry setup per (scatterer, sub-element) for all NB bins.  An element past N is
+// evaluated on element N - 1 with zero amplitude (no branch).  With the delta table, bin
+// qA picks the cubic piece and the later bins reuse it: bin qA + b moves u by b kap/dx,
+// small except within a few mm of the sub-element; up to half an interval outside the
+// piece the cubic is extrapolated (error <= 9 times the in-piece error), beyond that the
+// bin takes its own piece, and outside the table delta is evaluated directly.
+// o[c][b] = (Re, Im) of element e0 + c at bin qA + b.
+template <int NB, bool TAB, bool HAS_Y, int SINC, bool LINEAR>
+__device__ __forceinline__ void gen_two(const GreenConst &gc, const float4 *sub,
+                                        const float4 *tabs, const float4 &ps, int e0, float qA,
+                                        float (&o)[2][NB][2]) {
+    const int N = gc.N, nu = gc.nu;
+    const float w0 = e0 < N ? 1.0f : 0.0f, w1 = e0 + 1 < N ? 1.0f : 0.0f;
+    const int b0 = min(e0, N - 1) * nu, b1 = min(e0 + 1, N - 1) * nu;
+    const float t0 = gc.tab_x0 * gc.tab_inv_dx, tmax = (float)gc.tab_n - 0.5f;
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int b = 0; b < NB; ++b) o[c][b][0] = o[c][b][1] = 0.0f;
+    for (int mu = 0; mu < nu; ++mu) {
+        PairSetup P[2];
+        P[0] = pair_setup_f32<HAS_Y, LINEAR>(gc, sub[b0 + mu], ps.x, ps.y, ps.z, qA);
+        P[1] = pair_setup_f32<HAS_Y, LINEAR>(gc, sub[b1 + mu], ps.x, ps.y, ps.z, qA);
+        P[0].amp0 *= w0;
+        P[1].amp0 *= w1;
+        float kt[2] = {0.0f, 0.0f}, u[2] = {0.0f, 0.0f};
+        int ti[2] = {0, 0};
+        bool ok = TAB, far = false;
+        float tq[2] = {0.0f, 0.0f};
+        if (TAB) {
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                kt[c] = P[c].kap * gc.tab_inv_dx;
+                tq[c] = fmaf(qA, kt[c], -t0);
+                const float fl = floorf(fminf(fmaxf(tq[c], 0.0f), tmax));
+                ti[c] = (int)fl;
+                u[c] = tq[c] - fl;
+                const float ue = fmaf((float)(NB - 1), kt[c], u[c]);   // the last bin's u
+                ok = ok && u[c] >= 0.0f && u[c] <= 1.0f;
+                far = far || !(ue >= -0.5f && ue <= 1.5f);
+            }
+        }
+        float4 lo[2], hi[2];            // the pieces (index clamped: always a valid load)
+        if (TAB) {
+#pragma unroll
+            for (int c = 0; c < 2; ++c) { lo[c] = tabs[2 * ti[c]]; hi[c] = tabs[2 * ti[c] + 1]; }
+        }
+        // phase, absorption and sinc directivity of every bin (common to both delta forms)
+        float er[2][NB], ei[2][NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const float q = qA + (float)b;
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const float fr = df_frac_mul(q, P[c].u);
+                float sn, cs;
+                sincos_a(6.283185307179586f * fr, sn, cs);
+                float amp = P[c].amp0;
+                if (b >= 1) amp *= P[c].mstep;
+                if (b >= 2) amp *= P[c].mstep;
+                const float m = amp * sinc_f<SINC>(q * P[c].xb);
+                er[c][b] = cs * m;
+                ei[c][b] = sn * m;
+            }
+        }
+        float2 d[2][NB];
+        if (TAB) {
+#pragma unroll
+            for (int c = 0; c < 2; ++c)
+#pragma unroll
+                for (int b = 0; b < NB; ++b) d[c][b] = cubic_piece(lo[c], hi[c], fmaf((float)b, kt[c], u[c]));
+        }
+        if (TAB && NB > 1 && far) {
+            // a later bin moved more than half an interval past its piece (scatterers a few
+            // mm from the sub-element): it takes its own piece
+#pragma unroll
+            for (int c = 0; c < 2; ++c)
+#pragma unroll
+                for (int b = 1; b < NB; ++b) {
+                    const float ub = fmaf((float)b, kt[c], u[c]);
+                    if (!(ub >= -0.5f && ub <= 1.5f)) {
+                        const float tb = fmaf((float)b, kt[c], tq[c]);
+                        const float fl = floorf(fminf(fmaxf(tb, 0.0f), tmax));
+                        const int i = (int)fl;
+                        const float v = tb - fl;
+                        d[c][b] = cubic_piece(tabs[2 * i], tabs[2 * i + 1], v);
+                        ok = ok && v >= 0.0f && v <= 1.0f;
+                    }
+                }
+        }
+        if (!ok) {   // outside the table (within ~2 mm of the sub-element): Eq. 16 directly
+#pragma unroll
+            for (int c = 0; c < 2; ++c)
+#pragma unroll
+                for (int b = 0; b < NB; ++b) d[c][b] = delta_f<HAS_Y>(gc, P[c], qA + (float)b);
+        }
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                o[c][b][0] += er[c][b] * d[c][b].x - ei[c][b] * d[c][b].y;
+                o[c][b][1] += er[c][b] * d[c][b].y + ei[c][b] * d[c][b].x;
+            }
+    }
+}
+
+// One generation pass over a scatterer tile: every (scatterer, group of 8 elements) item
+// at bins qA .. qA + NB - 1.  Bin 0 goes as FP16/BF16 rows of the K-major tile A0, bin 1
+// to A1 when there are two shared-memory tile buffers (nbuf = 2); every further bin goes
+// to a tensor-memory stash slot (slot i at columns stash + i Np: row s in lane s, Re of the
+// 8 elements packed in columns 4 eg .. + 3, Im at Np/2 + 4 eg) until a buffer is free.
+// The lane rule holds by construction: item it has s = it mod 128 = 32 (warp mod 4) + lane.
+template <int NB, int NBUF, bool TAB, bool HAS_Y, int SINC, bool LINEAR>
+__device__ __forceinline__ void gen_tiles(const GreenConst &gc, const float4 *sub,
+                                          const float4 *tabs, const float4 *sc, int Np,
+                                          float qA, unsigned char *A0, unsigned char *A1,
+                                          uint32_t stash, bool bf16, int tid) {
+    constexpr int nbuf = NBUF < NB ? NBUF : NB;
+    const int K1 = 2 * Np;
+    const int n_groups = Np >> 3;
+    for (int it = tid; it < kSB * n_groups; it += kThreads) {
+        const int s = it & (kSB - 1), eg = it >> 7;
+        const float4 ps = sc[s];
+        uint32_t pk[NB][2][4];
+#pragma unroll
+        for (int jp = 0; jp < 4; ++jp) {
+            float o[2][NB][2];
+            gen_two<NB, TAB, HAS_Y, SINC, LINEAR>(gc, sub, tabs, ps, eg * 8 + 2 * jp, qA, o);
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                pk[b][0][jp] = h16x2(bf16, o[0][b][0], o[1][b][0]);
+                pk[b][1][jp] = h16x2(bf16, o[0][b][1], o[1][b][1]);
+            }
+        }
+        const uint32_t ta = stash + ((uint32_t)(s & ~31) << 16) + 4u * eg;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            if (b < nbuf) {
+                unsigned char *A = b ? A1 : A0;
+                *reinterpret_cast<uint4 *>(A + tc::kmajor_offset(s, eg * 8, K1)) =
+                    make_uint4(pk[b][0][0], pk[b][0][1], pk[b][0][2], pk[b][0][3]);
+                *reinterpret_cast<uint4 *>(A + tc::kmajor_offset(s, Np + eg * 8, K1)) =
+                    make_uint4(pk[b][1][0], pk[b][1][1], pk[b][1][2], pk[b][1][3]);
+            } else {
+                const uint32_t ts = ta + (uint32_t)((b - nbuf) * Np);
+                tc::tmem_st4(ts, pk[b][0][0], pk[b][0][1], pk[b][0][2], pk[b][0][3]);
+                tc::tmem_st4(ts + (uint32_t)(Np >> 1), pk[b][1][0], pk[b][1][1], pk[b][1][2], pk[b][1][3]);
+            }
+        }
+    }
+    if (NB > nbuf) tc::tmem_wait_st();
+}
+
+// Move a stashed bin from tensor memory into tile buffer A (same item-to-thread map as
+// gen_tiles, so every thread reads back the lanes and columns it wrote).
+__device__ __forceinline__ void unstash_tile(int Np, unsigned char *A, uint32_t slot, int tid) {
+    const int K1 = 2 * Np;
+    const int n_groups = Np >> 3;
+    for (int it = tid; it < kSB * n_groups; it += kThreads) {
+        const int s = it & (kSB - 1), eg = it >> 7;
+        const uint32_t ta = slot + ((uint32_t)(s & ~31) << 16) + 4u * eg;
+        uint32_t re[4], im[4];
+        tc::tmem_ld4(ta, re);
+        tc::tmem_ld4(ta + (uint32_t)(Np >> 1), im);
+        tc::tmem_wait_ld();
+        *reinterpret_cast<uint4 *>(A + tc::kmajor_offset(s, eg * 8, K1)) = make_uint4(re[0], re[1], re[2], re[3]);
+        *reinterpret_cast<uint4 *>(A + tc::kmajor_offset(s, Np + eg * 8, K1)) = make_uint4(im[0], im[1], im[2], im[3]);
+    }
+}
+
+}  // namespace
+
+template <bool HAS_Y, int SINC, bool LINEAR>
+__global__ void __launch_bounds__(kThreads, 1)
+k_tc_rf(const TcUnit *__restrict__ units, int n_units, int64_t n_items, int *counter, int *err,
+        int bf16) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    __shared__ TcUnit U;                  // the current item's unit
+
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem);          // 3 mbarriers
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + 24);
+    int *abort_flag = reinterpret_cast<int *>(smem + 28);
+    long long *s_item = reinterpret_cast<long long *>(smem + 32);
+    int *s_unit = reinterpret_cast<int *>(smem + 40);
+    unsigned char *dyn = smem + kHeader;
+    const uint32_t mbar_b1 = tc::smem_u32(&bars[0]);
+    const uint32_t mbar1 = tc::smem_u32(&bars[1]);
+    const uint32_t mbar2 = tc::smem_u32(&bars[2]);
+
+    if (tid == 0) {
+        tc::mbar_init(mbar_b1, 1);
+        tc::mbar_init(mbar1, 1);
+        tc::mbar_init(mbar2, 1);
+        tc::fence_mbar_init();
+        *abort_flag = 0;
+        *s_unit = -1;
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(tc::smem_u32(tslot), 512);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+
+    uint32_t ph_b1 = 0, ph1 = 0, ph2 = 0;
+    bool pending2 = false;     // an MMA2 commit not yet waited for
+    bool aborted = false;
+    bool b1_inflight = false;  // thread 0: a bulk copy into B1 not yet waited for
+    int cur_unit = -1;
+
+    auto wait_all = [&](uint32_t mbar, uint32_t parity) -> bool {
+        if (!tc::mbar_wait_bounded(mbar, parity, kMaxWait)) atomicExch(abort_flag, 1);
+        __syncthreads();
+        return *abort_flag == 0;
+    };
+
+    while (!aborted) {
+        // ---- next work item (dynamic: heavier units come first in the item order)
+        if (tid == 0) {
+            long long it = atomicAdd(counter, 1);
+            *s_item = it;
+            if (it < n_items) {
+                int lo = 0, hi = n_units - 1;     // last unit with item0 <= it
+                while (lo < hi) {
+                    int mid = (lo + hi + 1) >> 1;
+                    if (units[mid].item0 <= it) lo = mid; else hi = mid - 1;
+                }
+                *s_unit = lo;
+            }
+        }
+        __syncthreads();
+        const long long item = *s_item;
+        if (item >= n_items) break;
+        const int ui = *s_unit;
+        if (ui != cur_unit) {
+            if (pending2) {   // the previous unit's MMA2 may still read the tile buffers
+                if (!wait_all(mbar2, ph2)) { aborted = true; break; }
+                ph2 ^= 1;
+                pending2 = false;
+            }
+            const int nw = (int)(sizeof(TcUnit) / 4);
+            for (int i = tid; i < nw; i += kThreads)
+                reinterpret_cast<int *>(&U)[i] = reinterpret_cast<const int *>(&units[ui])[i];
+            __syncthreads();
+        }
+        const GreenConst gc = U.gc;   // register copy: the per-pair setup reads it often
+        const int N = gc.N, nu = gc.nu, M = gc.M, nq = gc.nq;
+        const int Np = U.Np, nN = U.nN, TG = U.TG, QB = U.QB, mh = U.mh, pair = U.pair;
+        const int G = U.G, T = U.T, nbuf = U.nbuf;
+        const int K1 = 2 * Np;
+        const size_t abytes = (size_t)kSB * K1 * 2;
+        unsigned char *A0 = dyn;
+        unsigned char *A1 = A0 + (nbuf == 2 ? abytes : 0);
+        unsigned char *B1 = A0 + nbuf * abytes;
+        unsigned char *B2 = B1 + (size_t)nN * K1 * 2;
+        float4 *sc = reinterpret_cast<float4 *>(B2 + (size_t)nN * 256 * 2);
+        float4 *sub = sc + kSB;                                            // compact records
+        float4 *tabs = sub + M;                                            // delta table
+        const bool use_tab = !HAS_Y && gc.tab_n > 0;
+        const uint32_t abuf0 = tc::smem_u32(A0), abuf1 = tc::smem_u32(A1);
+        const uint32_t b1s = tc::smem_u32(B1), b2s = tc::smem_u32(B2);
+        const uint32_t idesc1 = tc::idesc_f16(128, nN, bf16 != 0);
+        const uint32_t idesc2 = idesc1 | (1u << 15) | (1u << 16);   // A and B MN-major
+        const uint32_t b1_bytes = (uint32_t)nN * K1 * 2;
+        if (ui != cur_unit) {
+            for (int i = tid; i < M; i += kThreads) sub[i] = compact_sub(U.sub[i], LINEAR);
+            if (use_tab)
+                for (int i = tid; i < 2 * gc.tab_n; i += kThreads) tabs[i] = U.dtab[i];
+            cur_unit = ui;
+            __syncthreads();
+        }
+        auto issue_b1 = [&](int k, int g) {   // weights of bin k, transmit group g
+            if (tid == 0) {
+                tc::mbar_arrive_expect_tx(mbar_b1, b1_bytes);
+                tc::bulk_g2s(b1s, U.b1img + ((size_t)k * G + g) * nN * K1, b1_bytes, mbar_b1);
+                b1_inflight = true;
+            }
+        };
+
+        const int64_t li = item - U.item0;
+        const int bt = (int)(li % U.n_btiles), chunk = (int)(li / U.n_btiles);
+        const int k0 = bt * QB;
+        const int64_t tile0 = (int64_t)chunk * U.tiles_per_chunk;
+        const int64_t tile1 = std::min<int64_t>(tile0 + U.tiles_per_chunk, U.n_tiles);
+        const int step = pair + 1;                        // bins per generation pass
+        const uint32_t stash = tmem + (uint32_t)(nN * (1 + QB * G * mh));   // stash slots of Np columns
+        for (int64_t tile = tile0; tile < tile1 && !aborted; ++tile) {
+            for (int bp = 0; bp < QB && !aborted; bp += step) {
+                const int nb = min(step, QB - bp);
+                const int kA = min(k0 + bp, nq - 1);   // bins past the end repeat the last
+                issue_b1(kA, 0);                        // (their outputs are discarded)
+                if (pending2) {   // tile buffers and B2 still read by the last MMA2
+                    if (!wait_all(mbar2, ph2)) { aborted = true; break; }
+                    ph2 ^= 1;
+                    pending2 = false;
+                }
+                if (bp == 0) {    // new scatterer tile
+                    for (int i = tid; i < kSB; i += kThreads) {
+                        int64_t s = tile * kSB + i;
+                        sc[i] = s < U.S ? make_float4(U.x[s], (HAS_Y && U.y) ? U.y[s] : 0.f, U.z[s], U.rc[s])
+                                        : make_float4(0.f, 0.f, 1.f, 0.f);
+                    }
+                    __syncthreads();
+                }
+                // ---- Green's tiles of bins kA .. kA + nb - 1 (buffers A0, A1, then the stash)
+                const float qA = (float)(gc.q_lo + kA);
+                const bool tab = !HAS_Y && use_tab;
+#define SIMUS_GEN(NB_, NBUF_)                                                                     \
+    do {                                                                                          \
+        if (tab) gen_tiles<NB_, NBUF_, !HAS_Y, HAS_Y, SINC, LINEAR>(gc, sub, tabs, sc, Np, qA, A0, A1, stash, bf16 != 0, tid); \
+        else gen_tiles<NB_, NBUF_, false, HAS_Y, SINC, LINEAR>(gc, sub, tabs, sc, Np, qA, A0, A1, stash, bf16 != 0, tid);     \
+    } while (0)
+                if (nb == 3) {
+                    if (nbuf == 2) SIMUS_GEN(3, 2); else SIMUS_GEN(3, 1);
+                } else if (nb == 2) {
+                    if (nbuf == 2) SIMUS_GEN(2, 2); else SIMUS_GEN(2, 1);
+                } else {
+                    SIMUS_GEN(1, 1);
+                }
+#undef SIMUS_GEN
+                tc::fence_proxy_async_smem();
+                tc::fence_before_sync();
+                __syncthreads();
+                tc::fence_after_sync();
+
+                // every bin of the pass, every transmit group: MMA1 -> P' -> MMA2
+                for (int si = 0; si < nb * G && !aborted; ++si) {
+                    const int bi_ = si / G, g = si - bi_ * G;
+                    const int TGg = min(TG, T - g * TG);      // transmits of this group
+                    // a stashed bin goes to buffer (bi_ - nbuf) mod nbuf: with two buffers
+                    // the third bin into A0, whose last reader (MMA2 of the first bin)
+                    // completed before the second bin's first P'; with one buffer every
+                    // later bin into A0 once the previous bin's MMA2 has completed
+                    const int buf = bi_ < nbuf ? bi_ : (bi_ - nbuf) % nbuf;
+                    const uint32_t abase = buf ? abuf1 : abuf0;
+                    if (bi_ >= nbuf && g == 0) {
+                        if (nbuf == 1 && pending2) {
+                            if (!wait_all(mbar2, ph2)) { aborted = true; break; }
+                            ph2 ^= 1;
+                            pending2 = false;
+                        }
+                        unstash_tile(Np, buf ? A1 : A0, stash + (uint32_t)((bi_ - nbuf) * Np), tid);
+                        tc::fence_proxy_async_smem();
+                        tc::fence_before_sync();
+                        __syncthreads();
+                        tc::fence_after_sync();
+                    }
+                    // ---- MMA1: D1 = A * B1^T
+                    if (tid == 0) {
+                        if (!tc::mbar_wait_bounded(mbar_b1, ph_b1, kMaxWait)) {
+                            atomicExch(abort_flag, 1);
+                        } else {
+                            b1_inflight = false;
+                            tc::fence_after_sync();
+                            for (int j = 0; j < K1 / 16; ++j) {
+                                uint64_t ad = tc::smem_desc(abase + 256 * j, 128, 16 * K1);
+                                uint64_t bd = tc::smem_desc(b1s + 256 * j, 128, 16 * K1);
+                                tc::mma_f16(tmem, ad, bd, idesc1, j > 0);
+                            }
+                            tc::mma_commit(mbar1);
+                        }
+                    }
+                    ph_b1 ^= 1;
+                    if (!wait_all(mbar1, ph1)) { aborted = true; break; }
+                    ph1 ^= 1;
+                    tc::fence_after_sync();
+                    if (si + 1 < nb * G) {                     // B1 is free again
+                        const int sn = si + 1;
+                        issue_b1(min(k0 + bp + sn / G, nq - 1), sn % G);
+                    }
+                    if (pending2) {                            // B2 still read by MMA2
+                        if (!wait_all(mbar2, ph2)) { aborted = true; break; }
+                        ph2 ^= 1;
+                        pending2 = false;
+                    }
+                    // ---- P' = R_s P -> B2, MN-major (the 8 transmit rows of a core matrix
+                    // are contiguous for one scatterer): row 2t = (Re P' | -Im P'), row
+                    // 2t+1 = (Im P' | Re P') over K = (s | 128 + s), four 16-byte stores
+                    // per thread and 8 transmits
+                    {
+                        const int sp = warp & 3, cc = warp >> 2;
+                        const int s = sp * 32 + lane;
+                        const float R = sc[s].w;
+                        for (int c0 = cc * 16; c0 < nN; c0 += 64) {
+                            float v[16];
+                            tc::tmem_ld16(tmem + ((uint32_t)(sp * 32) << 16) + (uint32_t)c0, v);
+                            uint32_t w0[8], w1[8];
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) {
+                                const int t = (c0 >> 1) + i;
+                                float pr = 0.f, pi = 0.f;
+                                if (t < TGg) { pr = R * v[2 * i]; pi = R * v[2 * i + 1]; }
+                                w0[i] = h16x2(bf16 != 0, pr, pi);
+                                w1[i] = h16x2(bf16 != 0, -pi, pr);
+                            }
+                            const uint32_t nrow = (uint32_t)(nN >> 3);
+                            unsigned char *q0 = B2 + ((((uint32_t)(s >> 3) * nrow + (uint32_t)(c0 >> 3)) << 7) + ((s & 7) << 4));
+                            unsigned char *q1 = q0 + ((16u * nrow) << 7);        // k = 128 + s
+                            *reinterpret_cast<uint4 *>(q0) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+                            *reinterpret_cast<uint4 *>(q0 + 128) = make_uint4(w0[4], w0[5], w0[6], w0[7]);
+                            *reinterpret_cast<uint4 *>(q1) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+                            *reinterpret_cast<uint4 *>(q1 + 128) = make_uint4(w1[4], w1[5], w1[6], w1[7]);
+                        }
+                    }
+                    tc::fence_proxy_async_smem();
+                    tc::fence_before_sync();
+                    __syncthreads();
+                    tc::fence_after_sync();
+                    // ---- MMA2: D2[bin][half] (+)= A^T * B2^T, A^T the MN-major view of
+                    // the tile: k-slice j covers scatterers 16 (j mod 8) .. +15 of the Re
+                    // (j < 8) or Im (j >= 8) half.  In the no-swizzle MN-major form the
+                    // leading byte offset is the stride between K-adjacent core matrices
+                    // (scatterer groups, 16 K1 bytes) and the stride byte offset the one
+                    // between MN-adjacent core matrices (element groups, 128 bytes).
+                    if (tid == 0) {
+                        for (int h = 0; h < mh; ++h) {
+                            const uint32_t d2 = tmem + (uint32_t)(nN * (1 + ((bp + bi_) * G + g) * mh + h));
+                            for (int j = 0; j < 16; ++j) {
+                                const uint32_t a0 = abase + (uint32_t)((2 * (j & 7)) * 16 * K1)
+                                                  + (uint32_t)((j >> 3) * (Np / 8) * 128) + (uint32_t)(h * 16 * 128);
+                                uint64_t ad = tc::smem_desc(a0, 16 * K1, 128);
+                                uint64_t bd = tc::smem_desc(b2s + (uint32_t)(32 * nN * j), 16 * nN, 128);
+                                tc::mma_f16(d2, ad, bd, idesc2, (j > 0 || tile > tile0) ? 1u : 0u);
+                            }
+                        }
+                        tc::mma_commit(mbar2);
+                    }
+                    pending2 = true;
+                }
+            }
+        }
+        if (aborted) break;
+        if (pending2) {
+            if (!wait_all(mbar2, ph2)) { aborted = true; break; }
+            ph2 ^= 1;
+            pending2 = false;
+        }
+        tc::fence_after_sync();
+        // ---- partial spectra of this item: part[chunk][g TG + t][e][k]
+        {
+            const int sp = warp & 3, cc = warp >> 2;
+            for (int bg = 0; bg < QB * G; ++bg) {
+                const int b = bg / G, g = bg - b * G;
+                const int k = k0 + b;
+                const int TGg = min(TG, T - g * TG);
+                for (int h = 0; h < mh; ++h) {
+                    const int e = 128 * h + sp * 32 + lane;
+                    for (int c0 = cc * 16; c0 < nN; c0 += 64) {
+                        float v[16];
+                        tc::tmem_ld16(tmem + ((uint32_t)(sp * 32) << 16) +
+                                          (uint32_t)(nN * (1 + bg * mh + h) + c0), v);
+                        if (k < nq && e < N) {
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) {
+                                const int t = (c0 >> 1) + i;
+                                if (t < TGg)
+                                    U.part[(((size_t)chunk * T + g * TG + t) * N + e) * nq + k] =
+                                        make_float2(v[2 * i], v[2 * i + 1]);
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+    }
+    if (*abort_flag && tid == 0) {
+        atomicExch(err, SIMUS_ERR_TIMEOUT);
+        if (b1_inflight) tc::mbar_wait_bounded(mbar_b1, ph_b1, kMaxWait);   // own copy in flight
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, 512);
+}
+
+
+using TcKernelFn = void (*)(const TcUnit *, int, int64_t, int *, int *, int);
+// Instantiations, one translation unit each (see k_tc_rf_*.cu).
+TcKernelFn tc_kernel_y0_narrow(bool linear);
+TcKernelFn tc_kernel_y0_mid(bool linear);
+TcKernelFn tc_kernel_y0_wide(bool linear);
+TcKernelFn tc_kernel_y1_narrow(bool linear);
+TcKernelFn tc_kernel_y1_wide(bool linear);
+
+}  // namespace simus

@@ -1,0 +1,9 @@
+// k_tc_rf_y0_mid.cu -- instantiations of k_tc_rf for scatterers at Y = 0 and sinc
+// arguments up to 4.6 (every probe split by Eq. 21 with a bandwidth up to 75 %).
+#include "k_tc_kernel.cuh"
+
+namespace simus {
+TcKernelFn tc_kernel_y0_mid(bool linear) {
+    return linear ? k_tc_rf<false, 2, true> : k_tc_rf<false, 2, false>;
+}
+}  // namespace simus

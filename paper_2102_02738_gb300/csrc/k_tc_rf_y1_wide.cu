@@ -1,0 +1,9 @@
+// k_tc_rf_y1_wide.cu -- instantiations of k_tc_rf for scatterers off the azimuth plane
+// (Y != 0, delta with the Eq. 14 exponent) and sinc arguments beyond 3.2.
+#include "k_tc_kernel.cuh"
+
+namespace simus {
+TcKernelFn tc_kernel_y1_wide(bool linear) {
+    return linear ? k_tc_rf<true, 0, true> : k_tc_rf<true, 0, false>;
+}
+}  // namespace simus

@@ -256,7 +256,8 @@ GreenConst green_const(const simus_probe &pr, const simus_medium &md, int N, int
     gc.h = probe->two_d ? 1.0f : (float)probe->height;          // 2-D: no delta (Section V)
     gc.h2 = probe->two_d ? 0.0f : (float)(probe->height * probe->height);
     if (probe->two_d) gc.inv_rf = 0.0f;
-    gc.narrow = (2.0 * M_PI * K * b / nu) * q_max <= 3.19 ? 1 : 0;
+    const double x_max = (2.0 * M_PI * K * b / nu) * q_max;   // largest |k b sin(theta) / nu|
+    gc.narrow = x_max <= 3.19 ? 1 : (x_max <= 4.59 ? 2 : 0);
     gc.df = df;
     return gc;
 }
@@ -593,7 +594,8 @@ int tc_execute(simus_plan *owner, int n, simus_plan *const *plans, const simus_t
     std::vector<TcShape> sh(nl);
     size_t smem = 0;
     int n_units = 0;
-    bool has_y = false, narrow = true, linear = true;
+    bool has_y = false, linear = true;
+    int sinc_rank = 0;   // sinc range of the launch: 0 |x| <= 3.2, 1 |x| <= 4.6, 2 any
     for (int j = 0; j < nl; ++j) {
         const int i = live[j];
         const simus_plan *p = plans[i];
@@ -605,7 +607,7 @@ int tc_execute(simus_plan *owner, int n, simus_plan *const *plans, const simus_t
         smem = std::max(smem, sh[j].smem);
         n_units += 1;
         has_y = has_y || scs[i].y != nullptr;
-        narrow = narrow && p->gc.narrow;
+        sinc_rank = std::max(sinc_rank, p->gc.narrow == 1 ? 0 : (p->gc.narrow == 2 ? 1 : 2));
         linear = linear && p->probe.radius <= 0;
     }
     // workspace
@@ -674,7 +676,7 @@ int tc_execute(simus_plan *owner, int n, simus_plan *const *plans, const simus_t
             U.delays = txs[i].delays; U.apod = txs[i].apod;
             U.S = scs[i].n; U.n_tiles = s.n_tiles;
             U.T = txs[i].n_tx; U.G = s.n_groups; U.TG = s.TG;
-            U.Np = s.Np; U.mh = s.mh; U.pair = s.pair; U.QB = s.QB; U.nN = s.nN;
+            U.Np = s.Np; U.mh = s.mh; U.pair = s.pair; U.nbuf = s.nbuf; U.QB = s.QB; U.nN = s.nN;
             U.n_btiles = s.n_btiles; U.n_chunks = s.n_chunks; U.tiles_per_chunk = s.tiles_per_chunk;
             U.b1img = reinterpret_cast<uint16_t *>(base + b1_off[u]);
             U.part = reinterpret_cast<float2 *>(base + part_off[j]);
@@ -703,7 +705,8 @@ int tc_execute(simus_plan *owner, int n, simus_plan *const *plans, const simus_t
     if ((rc = check_cuda(cudaMemsetAsync(counter, 0, sizeof(int), st), "memset counter"))) return rc;
     stage_begin(owner, 1, st);
     rc = launch_tc_units(hu, d_units, n_units, n_items, smem, owner->path == SIMUS_PATH_TC_BF16, has_y,
-                         narrow, linear, owner->num_sms, counter, owner->d_err, st);
+                         sinc_rank == 0 ? 1 : (sinc_rank == 1 ? 2 : 0), linear, owner->num_sms,
+                         counter, owner->d_err, st);
     stage_end(owner, 1, st);
     if (rc) return rc;
     stage_begin(owner, 2, st);

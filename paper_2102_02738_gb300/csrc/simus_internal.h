@@ -30,7 +30,7 @@ struct GreenConst {
     float zeta;       // Eq. 39
     float h;          // element height (delta is evaluated as h * f(h^2 alpha))
     float h2;         // h^2
-    int32_t narrow;   // 1 if |k b / nu| <= 3.2 at every kept bin (polynomial sinc suffices)
+    int32_t narrow;   // sinc range at every kept bin: 1 |k b / nu| <= 3.2, 2 <= 4.6, 0 beyond
     int32_t tab_n;    // intervals of the delta table (0: none)
     float tab_x0;     // delta table: first abscissa of x = h^2 (k/2)(1/R_f - 1/r)
     float tab_inv_dx; // 1 / spacing
@@ -131,8 +131,9 @@ struct TcShape {
     int TG, n_groups;    // transmits per group, groups
     int nN;              // GEMM N of a group: 2 TG padded to 16
     int mh;              // receive GEMM M-halves: 1 (Np <= 128) or 2
-    int pair;            // bins per generation pass - 1: 0 one tile buffer, 1 two,
-                         // 2 two buffers and a tensor-memory stash for the third bin
+    int pair;            // bins per generation pass - 1 (0, 1, 2)
+    int nbuf;            // shared-memory tile buffers (1, 2); the other bins of a pass
+                         // wait in tensor-memory stash slots
     int tab_n;           // delta-table intervals staged in shared memory (0: direct delta)
     int QB;              // bins per work item
     int n_btiles;
@@ -155,7 +156,7 @@ struct TcUnit {
     int T, G, TG;                 // simulation transmits, transmit groups, group size
     int Np, nN, QB, mh, pair;
     int n_btiles, n_chunks, tiles_per_chunk;
-    int pad_;
+    int nbuf;                     // shared-memory tile buffers
     int64_t item0;                // first global item of this unit
     uint16_t *b1img;              // [nq][G][nN * 2Np]
     float2 *part;                 // [n_chunks][T][N][nq] of the simulation
@@ -163,7 +164,7 @@ struct TcUnit {
 // Launch the B1 image kernels of every unit and the persistent tensor-core kernel over
 // all items.  d_units: device copy of units (n_units), counter: zeroed device int.
 int launch_tc_units(const TcUnit *h_units, const TcUnit *d_units, int n_units, int64_t n_items,
-                    size_t smem, bool bf16, bool has_y, bool narrow, bool linear, int num_sms,
+                    size_t smem, bool bf16, bool has_y, int sinc_mode, bool linear, int num_sms,
                     int *counter, int *err, cudaStream_t st);
 
 // Adjoint (gradient) path, FP32.
