@@ -23,7 +23,8 @@ namespace simus {
 namespace {
 constexpr int kGThreads = 256;
 constexpr int kGQB = 2;     // bins per tile
-constexpr int kGSB = 8;     // scatterers per group
+constexpr int kGSBMax = 16; // scatterers per group (16, or 8 where shared memory is short)
+constexpr int kGRT = 2;     // transmits per thread in the contraction (register block)
 }  // namespace
 
 // lam[t][k][e] = H_k sum_j drf[t][e][j] exp(-2 pi i ((q_lo + k) j mod Nt) / Nt).
@@ -80,24 +81,26 @@ k_adjoint_dft(const float *__restrict__ drf, int N, int n_chan, int nq, int q_lo
     }
 }
 
+// Shared-memory rows of N complex values are padded to Nr = N + 1 so that rows of
+// different scatterers or transmits start in different banks.
 template <bool NARROW>
 __global__ void __launch_bounds__(kGThreads, 1)
 k_grad(const GreenConst gc, const SubElem *__restrict__ sub_g, const float *__restrict__ xg,
        const float *__restrict__ zg, const float *__restrict__ rcg, int64_t S, int64_t chunk_len,
-       int T, const float2 *__restrict__ cw, const float2 *__restrict__ lam,
+       int T, int SB, const float2 *__restrict__ cw, const float2 *__restrict__ lam,
        float *__restrict__ gpart /*[3][n_qtiles][S]*/, int n_qtiles,
        float2 *__restrict__ bpart /*[n_chunks][T][nq][N]*/) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int N = gc.N, nu = gc.nu, M = gc.M, nq = gc.nq;
+    const int N = gc.N, nu = gc.nu, M = gc.M, nq = gc.nq, Nr = N + 1;
     const int tid = threadIdx.x;
-    constexpr int QB = kGQB, SB = kGSB;
+    constexpr int QB = kGQB;
     float4 *sc = reinterpret_cast<float4 *>(smem_raw);              // [SB] (x, 0, z, R)
-    SubElem *sub = reinterpret_cast<SubElem *>(sc + SB);            // [M]
-    float2 *cwt = reinterpret_cast<float2 *>(sub + M);              // [QB][T][N]
-    float2 *lat = cwt + QB * T * N;                                 // [QB][T][N]
-    float2 *Bt = lat + QB * T * N;                                  // [QB][T][N]
-    float2 *Gt = Bt + QB * T * N;                                   // [3][QB][SB][N]
-    float2 *RA = Gt + 3 * QB * SB * N;                              // [QB][SB][T]
+    SubElem *sub = reinterpret_cast<SubElem *>(sc + kGSBMax);       // [M]
+    float2 *cwt = reinterpret_cast<float2 *>(sub + M);              // [QB][T][Nr]
+    float2 *lat = cwt + QB * T * Nr;                                // [QB][T][Nr]
+    float2 *Bt = lat + QB * T * Nr;                                 // [QB][T][N]
+    float2 *Gt = Bt + QB * T * N;                                   // [3][QB][SB][Nr]
+    float2 *RA = Gt + 3 * QB * SB * Nr;                             // [QB][SB][T]
     float *sg = reinterpret_cast<float *>(RA + QB * SB * T);        // [3][QB*SB*T]
     const int nit = QB * SB * T;
 
@@ -110,12 +113,20 @@ k_grad(const GreenConst gc, const SubElem *__restrict__ sub_g, const float *__re
     for (int i = tid; i < QB * T * N; i += kGThreads) {
         int j = i / (T * N), r = i - j * T * N, t = r / N, e = r - t * N, k = k0 + j;
         bool ok = k < nq;
-        cwt[i] = ok ? cw[((size_t)t * nq + k) * N + e] : make_float2(0.f, 0.f);
-        lat[i] = ok ? lam[((size_t)t * nq + k) * N + e] : make_float2(0.f, 0.f);
+        const int o = (j * T + t) * Nr + e;
+        cwt[o] = ok ? cw[((size_t)t * nq + k) * N + e] : make_float2(0.f, 0.f);
+        lat[o] = ok ? lam[((size_t)t * nq + k) * N + e] : make_float2(0.f, 0.f);
         Bt[i] = make_float2(0.f, 0.f);
     }
     const float q0 = (float)(gc.q_lo + k0);
-    const size_t plane = (size_t)QB * SB * N;
+    const size_t plane = (size_t)QB * SB * Nr;
+    // contraction work: (bin, scatterer, pair of transmits) items, each split over ks
+    // threads along the elements when there are fewer items than threads
+    const int TB = (T + kGRT - 1) / kGRT;
+    const int items = QB * SB * TB;
+    int ks = 1;
+    while (ks < 8 && items * ks * 2 <= kGThreads) ks *= 2;
+    const int units = items * ks;
 
     for (int64_t sb = s_begin; sb < s_end; sb += SB) {
         __syncthreads();
@@ -150,7 +161,7 @@ k_grad(const GreenConst gc, const SubElem *__restrict__ sub_g, const float *__re
             }
 #pragma unroll
             for (int j = 0; j < QB; ++j) {
-                const size_t o = ((size_t)j * SB + s) * N + e;
+                const size_t o = ((size_t)j * SB + s) * Nr + e;
                 Gt[o] = G[j];
                 Gt[plane + o] = GX[j];
                 Gt[2 * plane + o] = GZ[j];
@@ -158,35 +169,77 @@ k_grad(const GreenConst gc, const SubElem *__restrict__ sub_g, const float *__re
         }
         __syncthreads();
 
-        // 2. contractions per (bin, scatterer, transmit)
-        for (int it = tid; it < QB * SB * T; it += kGThreads) {
-            const int j = it / (SB * T), r = it - j * SB * T, s = r / T, t = r - s * T;
-            const float2 *g0 = Gt + ((size_t)j * SB + s) * N;
+        // 2. contractions per (bin, scatterer, transmit): P = C.G, A = L.G and the same
+        // with dG/dX, dG/dZ, as a register-blocked product (one scatterer, kGRT transmits)
+        for (int base = 0; base < units; base += kGThreads) {
+            const int w = base + tid;
+            const bool act = w < units;
+            const int it = act ? w / ks : 0, part = w - (w / ks) * ks;
+            const int j = it / (SB * TB), r = it - j * SB * TB, s = r / TB, tb = r - s * TB;
+            const int t0 = tb * kGRT;
+            const float2 *g0 = Gt + ((size_t)j * SB + s) * Nr;
             const float2 *g1 = g0 + plane, *g2 = g0 + 2 * plane;
-            const float2 *c = cwt + ((size_t)j * T + t) * N;
-            const float2 *l = lat + ((size_t)j * T + t) * N;
-            float Pr = 0, Pi = 0, Ar = 0, Ai = 0, Pxr = 0, Pxi = 0, Axr = 0, Axi = 0,
-                  Pzr = 0, Pzi = 0, Azr = 0, Azi = 0;
-            for (int e = 0; e < N; ++e) {
-                const float2 cc = c[e], ll = l[e], a = g0[e], bx = g1[e], bz = g2[e];
-                Pr = fmaf(cc.x, a.x, fmaf(-cc.y, a.y, Pr));
-                Pi = fmaf(cc.x, a.y, fmaf(cc.y, a.x, Pi));
-                Ar = fmaf(ll.x, a.x, fmaf(-ll.y, a.y, Ar));
-                Ai = fmaf(ll.x, a.y, fmaf(ll.y, a.x, Ai));
-                Pxr = fmaf(cc.x, bx.x, fmaf(-cc.y, bx.y, Pxr));
-                Pxi = fmaf(cc.x, bx.y, fmaf(cc.y, bx.x, Pxi));
-                Axr = fmaf(ll.x, bx.x, fmaf(-ll.y, bx.y, Axr));
-                Axi = fmaf(ll.x, bx.y, fmaf(ll.y, bx.x, Axi));
-                Pzr = fmaf(cc.x, bz.x, fmaf(-cc.y, bz.y, Pzr));
-                Pzi = fmaf(cc.x, bz.y, fmaf(cc.y, bz.x, Pzi));
-                Azr = fmaf(ll.x, bz.x, fmaf(-ll.y, bz.y, Azr));
-                Azi = fmaf(ll.x, bz.y, fmaf(ll.y, bz.x, Azi));
+            const float2 *cr[kGRT], *lr[kGRT];
+#pragma unroll
+            for (int dt = 0; dt < kGRT; ++dt) {
+                const int t = min(t0 + dt, T - 1);          // past T: a duplicate, discarded
+                cr[dt] = cwt + ((size_t)j * T + t) * Nr;
+                lr[dt] = lat + ((size_t)j * T + t) * Nr;
             }
-            const float R = sc[s].w;
-            sg[it] = Ar * Pr - Ai * Pi;                                             // dL/dR
-            sg[nit + it] = R * ((Ar * Pxr - Ai * Pxi) + (Pr * Axr - Pi * Axi));     // dL/dX
-            sg[2 * nit + it] = R * ((Ar * Pzr - Ai * Pzi) + (Pr * Azr - Pi * Azi)); // dL/dZ
-            RA[((size_t)j * SB + s) * T + t] = make_float2(R * Ar, R * Ai);
+            // acc[dt][type][0: C, 1: L][re, im]
+            float acc[kGRT][3][2][2];
+#pragma unroll
+            for (int dt = 0; dt < kGRT; ++dt)
+#pragma unroll
+                for (int y = 0; y < 3; ++y)
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) acc[dt][y][c][0] = acc[dt][y][c][1] = 0.f;
+#pragma unroll 2
+            for (int e = part; e < N; e += ks) {
+                const float2 a[3] = {g0[e], g1[e], g2[e]};
+#pragma unroll
+                for (int dt = 0; dt < kGRT; ++dt) {
+                    const float2 cc = cr[dt][e], ll = lr[dt][e];
+#pragma unroll
+                    for (int y = 0; y < 3; ++y) {
+                        acc[dt][y][0][0] = fmaf(cc.x, a[y].x, fmaf(-cc.y, a[y].y, acc[dt][y][0][0]));
+                        acc[dt][y][0][1] = fmaf(cc.x, a[y].y, fmaf(cc.y, a[y].x, acc[dt][y][0][1]));
+                        acc[dt][y][1][0] = fmaf(ll.x, a[y].x, fmaf(-ll.y, a[y].y, acc[dt][y][1][0]));
+                        acc[dt][y][1][1] = fmaf(ll.x, a[y].y, fmaf(ll.y, a[y].x, acc[dt][y][1][1]));
+                    }
+                }
+            }
+            for (int o = 1; o < ks; o <<= 1) {              // ks adjacent lanes share an item
+#pragma unroll
+                for (int dt = 0; dt < kGRT; ++dt)
+#pragma unroll
+                    for (int y = 0; y < 3; ++y)
+#pragma unroll
+                        for (int c = 0; c < 2; ++c) {
+                            acc[dt][y][c][0] += __shfl_xor_sync(0xffffffffu, acc[dt][y][c][0], o);
+                            acc[dt][y][c][1] += __shfl_xor_sync(0xffffffffu, acc[dt][y][c][1], o);
+                        }
+            }
+            if (act && part == 0) {
+                const float R = sc[s].w;
+#pragma unroll
+                for (int dt = 0; dt < kGRT; ++dt) {
+                    const int t = t0 + dt;
+                    if (t < T) {
+                        const float Pr = acc[dt][0][0][0], Pi = acc[dt][0][0][1];
+                        const float Ar = acc[dt][0][1][0], Ai = acc[dt][0][1][1];
+                        const float Pxr = acc[dt][1][0][0], Pxi = acc[dt][1][0][1];
+                        const float Axr = acc[dt][1][1][0], Axi = acc[dt][1][1][1];
+                        const float Pzr = acc[dt][2][0][0], Pzi = acc[dt][2][0][1];
+                        const float Azr = acc[dt][2][1][0], Azi = acc[dt][2][1][1];
+                        const int o = (j * SB + s) * T + t;
+                        sg[o] = Ar * Pr - Ai * Pi;                                             // dL/dR
+                        sg[nit + o] = R * ((Ar * Pxr - Ai * Pxi) + (Pr * Axr - Pi * Axi));     // dL/dX
+                        sg[2 * nit + o] = R * ((Ar * Pzr - Ai * Pzi) + (Pr * Azr - Pi * Azi)); // dL/dZ
+                        RA[o] = make_float2(R * Ar, R * Ai);
+                    }
+                }
+            }
         }
         __syncthreads();
 
@@ -196,7 +249,7 @@ k_grad(const GreenConst gc, const SubElem *__restrict__ sub_g, const float *__re
             float2 b = Bt[i];
             for (int s = 0; s < SB; ++s) {
                 const float2 ra = RA[((size_t)j * SB + s) * T + t];
-                const float2 a = Gt[((size_t)j * SB + s) * N + e];
+                const float2 a = Gt[((size_t)j * SB + s) * Nr + e];
                 b.x = fmaf(ra.x, a.x, fmaf(-ra.y, a.y, b.x));
                 b.y = fmaf(ra.x, a.y, fmaf(ra.y, a.x, b.y));
             }
@@ -264,17 +317,22 @@ GradGeom grad_geometry(const simus_plan *p, int T, int64_t S) {
     GradGeom g{};
     g.ok = (int64_t)T * p->N <= 2048;
     g.n_qtiles = (p->nq + kGQB - 1) / kGQB;
+    const size_t Nr = (size_t)p->N + 1;
+    auto smem_for = [&](int SB) {
+        return sizeof(float4) * kGSBMax + sizeof(SubElem) * p->M
+             + sizeof(float2) * (size_t)kGQB * T * Nr * 2 + sizeof(float2) * (size_t)kGQB * T * p->N
+             + sizeof(float2) * (size_t)3 * kGQB * SB * Nr
+             + sizeof(float2) * (size_t)kGQB * SB * T + sizeof(float) * 3 * kGQB * SB * T;
+    };
+    g.SB = smem_for(kGSBMax) <= 227 * 1024 ? kGSBMax : 8;
     int64_t want = (int64_t)p->num_sms * 4;
     int64_t chunks = std::max<int64_t>(1, (want + g.n_qtiles - 1) / g.n_qtiles);
-    chunks = std::min<int64_t>(chunks, std::max<int64_t>(1, S / (kGSB * 16)));
+    chunks = std::min<int64_t>(chunks, std::max<int64_t>(1, S / (g.SB * 16)));
     int64_t len = (S + chunks - 1) / chunks;
-    len = ((len + kGSB - 1) / kGSB) * kGSB;
-    g.chunk_len = std::max<int64_t>(len, kGSB);
+    len = ((len + g.SB - 1) / g.SB) * g.SB;
+    g.chunk_len = std::max<int64_t>(len, g.SB);
     g.n_chunks = (int)((S + g.chunk_len - 1) / g.chunk_len);
-    g.smem = sizeof(float4) * kGSB + sizeof(SubElem) * p->M
-           + sizeof(float2) * (size_t)kGQB * T * p->N * 3
-           + sizeof(float2) * (size_t)3 * kGQB * kGSB * p->N
-           + sizeof(float2) * (size_t)kGQB * kGSB * T + sizeof(float) * 3 * kGQB * kGSB * T;
+    g.smem = smem_for(g.SB);
     g.ok = g.ok && g.smem <= 227 * 1024;
     return g;
 }
@@ -295,7 +353,7 @@ int launch_grad(const simus_plan *p, const GradGeom &g, const simus_scat *sc, in
     if (e != cudaSuccess) return check_cuda(e, "k_grad smem attribute");
     dim3 grid(g.n_qtiles, g.n_chunks);
     kern<<<grid, kGThreads, g.smem, st>>>(p->gc, p->d_sub, sc->x, sc->z, sc->rc, sc->n, g.chunk_len,
-                                          T, cw, lam, gpart, g.n_qtiles, bpart);
+                                          T, g.SB, cw, lam, gpart, g.n_qtiles, bpart);
     count_launches(1);
     return check_cuda(cudaGetLastError(), "k_grad launch");
 }

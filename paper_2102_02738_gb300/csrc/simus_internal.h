@@ -171,6 +171,7 @@ int launch_tc_units(const TcUnit *h_units, const TcUnit *d_units, int n_units, i
 struct GradGeom {
     bool ok;             // T * N <= 2048 and the shared-memory tiles fit
     int n_qtiles, n_chunks;
+    int SB;              // scatterers per group (16, or 8 where shared memory is short)
     int64_t chunk_len;
     size_t smem;
 };
