@@ -21,7 +21,7 @@
 namespace simus {
 
 namespace {
-constexpr int kGThreads = 256;
+constexpr int kGThreads = 384;  // 12 warps: the register budget of the generation allows it
 constexpr int kGQB = 2;     // bins per tile
 constexpr int kGSBMax = 16; // scatterers per group (16, or 8 where shared memory is short)
 constexpr int kGRT = 2;     // transmits per thread in the contraction (register block)
@@ -243,17 +243,28 @@ k_grad(const GreenConst gc, const SubElem *__restrict__ sub_g, const float *__re
         }
         __syncthreads();
 
-        // 3. B_q(t, e) += sum_s R_s A_t G_e ; per-scatterer gradients of this bin tile
-        for (int i = tid; i < QB * T * N; i += kGThreads) {
-            const int j = i / (T * N), r = i - j * T * N, t = r / N, e = r - t * N;
-            float2 b = Bt[i];
+        // 3. B_q(t, e) += sum_s R_s A_t G_e (four elements per thread); per-scatterer
+        // gradients of this bin tile
+        const int N4 = (N + 3) >> 2;
+        for (int i = tid; i < QB * T * N4; i += kGThreads) {
+            const int j = i / (T * N4), r = i - j * T * N4, t = r / N4, e0 = (r - t * N4) * 4;
+            float2 b[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) b[u] = make_float2(0.f, 0.f);
             for (int s = 0; s < SB; ++s) {
                 const float2 ra = RA[((size_t)j * SB + s) * T + t];
-                const float2 a = Gt[((size_t)j * SB + s) * Nr + e];
-                b.x = fmaf(ra.x, a.x, fmaf(-ra.y, a.y, b.x));
-                b.y = fmaf(ra.x, a.y, fmaf(ra.y, a.x, b.y));
+                const float2 *g = Gt + ((size_t)j * SB + s) * Nr + e0;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const float2 a = g[u];     // past N: the padding column or the next row, unused
+                    b[u].x = fmaf(ra.x, a.x, fmaf(-ra.y, a.y, b[u].x));
+                    b[u].y = fmaf(ra.x, a.y, fmaf(ra.y, a.x, b[u].y));
+                }
             }
-            Bt[i] = b;
+            float2 *bt = Bt + ((size_t)j * T + t) * N + e0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (e0 + u < N) { bt[u].x += b[u].x; bt[u].y += b[u].y; }
         }
         if (tid < 3 * SB) {       // fixed-order sum over (bin, transmit): reproducible
             const int which = tid / SB, s = tid - which * SB;

@@ -1,0 +1,234 @@
+// k_plain_mt.cu -- plain FP32 path for several transmits: the Green's tile of a group of
+// scatterers is generated once per bin and contracted against every transmit, instead
+// of being regenerated per transmit.
+//
+// Block tile: kMtQB consecutive kept bins x one chunk of scatterers x all N elements x all
+// T transmits (T N <= 2048).  For each group of SB scatterers the block
+//   1. generates G_e(q, s, e) = sum_mu g(q, s, (e, mu)) (Eq. 17/20/33/39/40) for the
+//      kMtQB x SB x N tile into shared memory, one geometry setup (double-float distance
+//      and phase rate) per (scatterer, sub-element) for all kMtQB bins;
+//   2. forms P_t(q, s) = sum_e C_t(q, e) G_e(q, s, e) (Eq. 29) as a register-blocked
+//      product (two scatterers x two transmits per thread) and scales it by R_s;
+//   3. accumulates RF_q(t, e) += sum_s G_e(q, s, e) R_s P_t(q, s) (Eq. 30-32) in shared
+//      memory (four elements per thread).
+// Rows of N complex values are padded to N + 1 so that rows start in different banks.
+// The chunk's partial spectrum goes to part[chunk][t][e][k]; chunks are summed in a fixed
+// order by the reduction kernel, so results are bitwise reproducible.
+#include <algorithm>
+#include <type_traits>
+
+#include "green.cuh"
+#include "simus_internal.h"
+
+namespace simus {
+
+namespace {
+constexpr int kMtThreads = 384;
+constexpr int kMtQB = 4;        // bins per tile
+constexpr int kMtSBMax = 32;    // scatterers per group (32, 16 or 8: what shared memory allows)
+}  // namespace
+
+template <bool HAS_Y, int SINC>
+__global__ void __launch_bounds__(kMtThreads, 1)
+k_plain_mt(const GreenConst gc, const SubElem *__restrict__ sub_g, const float *__restrict__ xg,
+           const float *__restrict__ yg, const float *__restrict__ zg,
+           const float *__restrict__ rcg, int64_t S, int64_t chunk_len, int SB, int T,
+           const float2 *__restrict__ cw, float2 *__restrict__ part) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int QB = kMtQB;
+    const int N = gc.N, nu = gc.nu, M = gc.M, nq = gc.nq, Nr = N + 1;
+    const int tid = threadIdx.x;
+    float4 *sc = reinterpret_cast<float4 *>(smem_raw);              // [kMtSBMax] (x, y, z, R)
+    SubElem *sub = reinterpret_cast<SubElem *>(sc + kMtSBMax);      // [M]
+    float2 *cwt = reinterpret_cast<float2 *>(sub + M);              // [QB][T][Nr]
+    float2 *rft = cwt + QB * T * Nr;                                // [QB][T][N]
+    float2 *Gt = rft + QB * T * N;                                  // [QB][SB][Nr]
+    float2 *RP = Gt + QB * SB * Nr;                                 // [QB][SB][T]
+
+    const int qt = blockIdx.x, chunk = blockIdx.y;
+    const int k0 = qt * QB;
+    const int64_t s_begin = (int64_t)chunk * chunk_len;
+    const int64_t s_end = min(S, s_begin + chunk_len);
+
+    for (int i = tid; i < M; i += kMtThreads) sub[i] = sub_g[i];
+    for (int i = tid; i < QB * T * N; i += kMtThreads) {
+        const int j = i / (T * N), r = i - j * T * N, t = r / N, e = r - t * N, k = k0 + j;
+        cwt[(j * T + t) * Nr + e] = k < nq ? cw[((size_t)t * nq + k) * N + e] : make_float2(0.f, 0.f);
+        rft[i] = make_float2(0.f, 0.f);
+    }
+    const float q0 = (float)(gc.q_lo + k0);
+    // contraction work: (bin, scatterer pair, transmit pair) items, each split over ks
+    // threads along the elements when there are fewer items than threads
+    const int SP = (SB + 1) >> 1, TP = (T + 1) >> 1;
+    const int items = QB * SP * TP;
+    int ks = 1;
+    while (ks < 8 && items * ks * 2 <= kMtThreads) ks *= 2;
+    const int units = items * ks;
+    const int N4 = (N + 3) >> 2;
+
+    for (int64_t sb = s_begin; sb < s_end; sb += SB) {
+        __syncthreads();
+        if (tid < SB) {
+            const int64_t s = sb + tid;
+            sc[tid] = s < s_end ? make_float4(xg[s], HAS_Y ? yg[s] : 0.f, zg[s], rcg[s])
+                                : make_float4(0.f, 0.f, 1.f, 0.f);
+        }
+        __syncthreads();
+
+        // 1. Green's tile of the QB bins
+        for (int pr = tid; pr < SB * N; pr += kMtThreads) {
+            const int s = pr / N, e = pr - s * N;
+            const float4 ps = sc[s];
+            float2 G[QB];
+#pragma unroll
+            for (int j = 0; j < QB; ++j) G[j] = make_float2(0.f, 0.f);
+            for (int mu = 0; mu < nu; ++mu) {
+                const PairSetup P = pair_setup<HAS_Y>(gc, sub[e * nu + mu], ps.x, ps.y, ps.z, q0);
+                float amp = P.amp0;
+#pragma unroll
+                for (int j = 0; j < QB; ++j) {
+                    const float q = q0 + (float)j;
+                    const float fr = df_frac_mul(q, P.u);
+                    float sn, cs;
+                    sincos_a(6.283185307179586f * fr, sn, cs);
+                    const float m = amp * sinc_f<SINC>(q * P.xb);
+                    const float2 d = delta_f<HAS_Y>(gc, P, q);
+                    const float er = cs * m, ei = sn * m;
+                    G[j].x += er * d.x - ei * d.y;
+                    G[j].y += er * d.y + ei * d.x;
+                    amp *= P.mstep;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < QB; ++j) Gt[(j * SB + s) * Nr + e] = G[j];
+        }
+        __syncthreads();
+
+        // 2. P_t = sum_e C_t G_e for two scatterers x two transmits per item, then R_s P
+        for (int base = 0; base < units; base += kMtThreads) {
+            const int w = base + tid;
+            const bool act = w < units;
+            const int it = act ? w / ks : 0, part_ = w - (w / ks) * ks;
+            const int j = it / (SP * TP), r = it - j * SP * TP, sp = r / TP, tp = r - sp * TP;
+            const int s0 = 2 * sp, t0 = 2 * tp;
+            const float2 *g[2], *c[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                g[u] = Gt + (j * SB + min(s0 + u, SB - 1)) * Nr;        // past the group /
+                c[u] = cwt + (j * T + min(t0 + u, T - 1)) * Nr;         // T: duplicates, dropped
+            }
+            float acc[2][2][2];   // [scatterer][transmit][re, im]
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+#pragma unroll
+                for (int b = 0; b < 2; ++b) acc[a][b][0] = acc[a][b][1] = 0.f;
+#pragma unroll 4
+            for (int e = part_; e < N; e += ks) {
+                const float2 ga = g[0][e], gb = g[1][e], ca = c[0][e], cb = c[1][e];
+                acc[0][0][0] = fmaf(ca.x, ga.x, fmaf(-ca.y, ga.y, acc[0][0][0]));
+                acc[0][0][1] = fmaf(ca.x, ga.y, fmaf(ca.y, ga.x, acc[0][0][1]));
+                acc[0][1][0] = fmaf(cb.x, ga.x, fmaf(-cb.y, ga.y, acc[0][1][0]));
+                acc[0][1][1] = fmaf(cb.x, ga.y, fmaf(cb.y, ga.x, acc[0][1][1]));
+                acc[1][0][0] = fmaf(ca.x, gb.x, fmaf(-ca.y, gb.y, acc[1][0][0]));
+                acc[1][0][1] = fmaf(ca.x, gb.y, fmaf(ca.y, gb.x, acc[1][0][1]));
+                acc[1][1][0] = fmaf(cb.x, gb.x, fmaf(-cb.y, gb.y, acc[1][1][0]));
+                acc[1][1][1] = fmaf(cb.x, gb.y, fmaf(cb.y, gb.x, acc[1][1][1]));
+            }
+            for (int o = 1; o < ks; o <<= 1) {              // ks adjacent lanes share an item
+#pragma unroll
+                for (int a = 0; a < 2; ++a)
+#pragma unroll
+                    for (int b = 0; b < 2; ++b) {
+                        acc[a][b][0] += __shfl_xor_sync(0xffffffffu, acc[a][b][0], o);
+                        acc[a][b][1] += __shfl_xor_sync(0xffffffffu, acc[a][b][1], o);
+                    }
+            }
+            if (act && part_ == 0) {
+#pragma unroll
+                for (int a = 0; a < 2; ++a)
+#pragma unroll
+                    for (int b = 0; b < 2; ++b)
+                        if (s0 + a < SB && t0 + b < T) {
+                            const float R = sc[s0 + a].w;
+                            RP[(j * SB + s0 + a) * T + t0 + b] = make_float2(R * acc[a][b][0], R * acc[a][b][1]);
+                        }
+            }
+        }
+        __syncthreads();
+
+        // 3. RF_q(t, e) += sum_s G_e R_s P_t, four elements per thread
+        for (int i = tid; i < QB * T * N4; i += kMtThreads) {
+            const int j = i / (T * N4), r = i - j * T * N4, t = r / N4, e0 = (r - t * N4) * 4;
+            float2 a[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) a[u] = make_float2(0.f, 0.f);
+            for (int s = 0; s < SB; ++s) {
+                const float2 rp = RP[(j * SB + s) * T + t];
+                const float2 *gg = Gt + (j * SB + s) * Nr + e0;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const float2 v = gg[u];    // past N: padding or the next row, unused
+                    a[u].x = fmaf(v.x, rp.x, fmaf(-v.y, rp.y, a[u].x));
+                    a[u].y = fmaf(v.x, rp.y, fmaf(v.y, rp.x, a[u].y));
+                }
+            }
+            float2 *rr = rft + (j * T + t) * N + e0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (e0 + u < N) { rr[u].x += a[u].x; rr[u].y += a[u].y; }
+        }
+    }
+    __syncthreads();
+    for (int i = tid; i < QB * T * N; i += kMtThreads) {   // bins fastest: runs of QB in part
+        const int j = i % QB, r = i / QB, e = r % N, t = r / N, k = k0 + j;
+        if (k < nq) part[(((size_t)chunk * T + t) * N + e) * nq + k] = rft[(j * T + t) * N + e];
+    }
+}
+
+static size_t plain_mt_smem(const simus_plan *p, int T, int SB) {
+    const size_t Nr = (size_t)p->N + 1;
+    return sizeof(float4) * kMtSBMax + sizeof(SubElem) * p->M
+         + sizeof(float2) * (size_t)kMtQB * T * (Nr + p->N) + sizeof(float2) * (size_t)kMtQB * SB * Nr
+         + sizeof(float2) * (size_t)kMtQB * SB * T;
+}
+
+PlainGeom plain_mt_geometry(const simus_plan *p, int T, int64_t S) {
+    PlainGeom g{};
+    g.QB = kMtQB;
+    g.SB = 0;
+    if (T < 2 || (int64_t)T * p->N > 2048) return g;
+    for (int sb = kMtSBMax; sb >= 8 && !g.SB; sb /= 2)
+        if (plain_mt_smem(p, T, sb) <= 227 * 1024) g.SB = sb;
+    if (!g.SB) return g;
+    g.n_qtiles = (p->nq + g.QB - 1) / g.QB;
+    // about four blocks per SM in total, chunks of at least eight groups
+    const int64_t want = (int64_t)p->num_sms * 4;
+    int64_t chunks = std::max<int64_t>(1, (want + g.n_qtiles - 1) / g.n_qtiles);
+    chunks = std::min<int64_t>(chunks, std::max<int64_t>(1, S / ((int64_t)g.SB * 8)));
+    int64_t len = (S + chunks - 1) / chunks;
+    len = ((len + g.SB - 1) / g.SB) * g.SB;
+    g.chunk_len = std::max<int64_t>(len, g.SB);
+    g.n_chunks = (int)((S + g.chunk_len - 1) / g.chunk_len);
+    g.smem = plain_mt_smem(p, T, g.SB);
+    return g;
+}
+
+int launch_plain_mt(const simus_plan *p, const PlainGeom &g, const simus_scat *sc, int T,
+                    const float2 *cw, float2 *part, cudaStream_t st) {
+    const bool has_y = sc->y != nullptr;
+    const int mode = p->gc.narrow;
+    auto pick = [&](auto hy) {
+        constexpr bool HY = decltype(hy)::value;
+        return mode == 1 ? k_plain_mt<HY, 1> : (mode == 2 ? k_plain_mt<HY, 2> : k_plain_mt<HY, 0>);
+    };
+    auto kern = has_y ? pick(std::true_type{}) : pick(std::false_type{});
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
+    if (e != cudaSuccess) return check_cuda(e, "k_plain_mt smem attribute");
+    dim3 grid(g.n_qtiles, g.n_chunks);
+    kern<<<grid, kMtThreads, g.smem, st>>>(p->gc, p->d_sub, sc->x, sc->y, sc->z, sc->rc, sc->n,
+                                          g.chunk_len, g.SB, T, cw, part);
+    count_launches(1);
+    return check_cuda(cudaGetLastError(), "k_plain_mt launch");
+}
+
+}  // namespace simus

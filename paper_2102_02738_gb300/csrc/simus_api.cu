@@ -539,7 +539,9 @@ namespace {
 int plain_run(simus_plan *p, const simus_tx *tx, const simus_scat *sc, float2 *spec_out,
               float *rf, cudaStream_t st) {
     const int T = tx->n_tx, n_chan = T * p->N;
-    const PlainGeom g = plain_geometry(p, T, sc->n);
+    const PlainGeom gm = plain_mt_geometry(p, T, sc->n);   // several transmits: one tile per bin
+    const bool mt = gm.SB > 0;
+    const PlainGeom g = mt ? gm : plain_geometry(p, T, sc->n);
     const size_t w_b = align256(sizeof(float2) * (size_t)T * p->nq * p->N);
     const size_t part_b = align256(sizeof(float2) * (size_t)g.n_chunks * n_chan * p->nq);
     const size_t spec_b = spec_out ? 0 : align256(sizeof(float2) * (size_t)n_chan * p->nq);
@@ -554,7 +556,8 @@ int plain_run(simus_plan *p, const simus_tx *tx, const simus_scat *sc, float2 *s
     if ((rc = launch_tx_weights(p, tx, cw, st))) return rc;
     stage_end(p, 0, st);
     stage_begin(p, 1, st);
-    if ((rc = launch_plain(p, g, sc, T, cw, part, st))) return rc;
+    if ((rc = mt ? launch_plain_mt(p, g, sc, T, cw, part, st) : launch_plain(p, g, sc, T, cw, part, st)))
+        return rc;
     stage_end(p, 1, st);
     stage_begin(p, 2, st);
     if ((rc = launch_reduce_spectrum(p, part, g.n_chunks, n_chan, spec, st))) return rc;
