@@ -46,9 +46,9 @@ extern "C" {
 
 /* Contraction path chosen at plan creation.
  *   PLAIN_F32 : Green's terms and every contraction in FP32 on the CUDA cores; with
- *               several transmits and T N <= 2048 a Green's tile is generated once per
- *               bin and contracted against every transmit, otherwise it is recomputed
- *               for each transmit.
+ *               several transmits a Green's tile is generated once per bin and
+ *               contracted against every transmit where its operands fit shared memory
+ *               (T N up to ~6,000), otherwise it is recomputed for each transmit.
  *   TC_F16    : Green's terms generated once per (bin, scatterer, element) in FP32,
  *               rounded to FP16, and both contractions (transmit sum Eq. 29 and
  *               receive sum Eq. 32) run on the tcgen05 tensor cores with FP32

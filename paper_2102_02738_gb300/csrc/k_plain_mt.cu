@@ -2,11 +2,12 @@
 // scatterers is generated once per bin and contracted against every transmit, instead
 // of being regenerated per transmit.
 //
-// Block tile: kMtQB consecutive kept bins x one chunk of scatterers x all N elements x all
-// T transmits (T N <= 2048).  For each group of SB scatterers the block
+// Block tile: QB (4 or 2) consecutive kept bins x one chunk of scatterers x all N elements x
+// all T transmits, as large as shared memory allows.  For each group of SB scatterers the
+// block
 //   1. generates G_e(q, s, e) = sum_mu g(q, s, (e, mu)) (Eq. 17/20/33/39/40) for the
-//      kMtQB x SB x N tile into shared memory, one geometry setup (double-float distance
-//      and phase rate) per (scatterer, sub-element) for all kMtQB bins;
+//      QB x SB x N tile into shared memory, one geometry setup (double-float distance
+//      and phase rate) per (scatterer, sub-element) for all QB bins;
 //   2. forms P_t(q, s) = sum_e C_t(q, e) G_e(q, s, e) (Eq. 29) as a register-blocked
 //      product (two scatterers x two transmits per thread) and scales it by R_s;
 //   3. accumulates RF_q(t, e) += sum_s G_e(q, s, e) R_s P_t(q, s) (Eq. 30-32) in shared
@@ -24,18 +25,17 @@ namespace simus {
 
 namespace {
 constexpr int kMtThreads = 384;
-constexpr int kMtQB = 4;        // bins per tile
+constexpr int kMtQBMax = 4;     // bins per tile (4, or 2 for many transmits)
 constexpr int kMtSBMax = 32;    // scatterers per group (32, 16 or 8: what shared memory allows)
 }  // namespace
 
-template <bool HAS_Y, int SINC>
+template <int QB, bool HAS_Y, int SINC>
 __global__ void __launch_bounds__(kMtThreads, 1)
 k_plain_mt(const GreenConst gc, const SubElem *__restrict__ sub_g, const float *__restrict__ xg,
            const float *__restrict__ yg, const float *__restrict__ zg,
            const float *__restrict__ rcg, int64_t S, int64_t chunk_len, int SB, int T,
            const float2 *__restrict__ cw, float2 *__restrict__ part) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    constexpr int QB = kMtQB;
     const int N = gc.N, nu = gc.nu, M = gc.M, nq = gc.nq, Nr = N + 1;
     const int tid = threadIdx.x;
     float4 *sc = reinterpret_cast<float4 *>(smem_raw);              // [kMtSBMax] (x, y, z, R)
@@ -185,20 +185,21 @@ k_plain_mt(const GreenConst gc, const SubElem *__restrict__ sub_g, const float *
     }
 }
 
-static size_t plain_mt_smem(const simus_plan *p, int T, int SB) {
+static size_t plain_mt_smem(const simus_plan *p, int T, int QB, int SB) {
     const size_t Nr = (size_t)p->N + 1;
     return sizeof(float4) * kMtSBMax + sizeof(SubElem) * p->M
-         + sizeof(float2) * (size_t)kMtQB * T * (Nr + p->N) + sizeof(float2) * (size_t)kMtQB * SB * Nr
-         + sizeof(float2) * (size_t)kMtQB * SB * T;
+         + sizeof(float2) * (size_t)QB * T * (Nr + p->N) + sizeof(float2) * (size_t)QB * SB * Nr
+         + sizeof(float2) * (size_t)QB * SB * T;
 }
 
 PlainGeom plain_mt_geometry(const simus_plan *p, int T, int64_t S) {
     PlainGeom g{};
-    g.QB = kMtQB;
     g.SB = 0;
-    if (T < 2 || (int64_t)T * p->N > 2048) return g;
-    for (int sb = kMtSBMax; sb >= 8 && !g.SB; sb /= 2)
-        if (plain_mt_smem(p, T, sb) <= 227 * 1024) g.SB = sb;
+    if (T < 2) return g;
+    // the largest tile (bins first, then scatterers per group) whose operands fit
+    for (int qb = kMtQBMax; qb >= 2 && !g.SB; qb /= 2)
+        for (int sb = kMtSBMax; sb >= 8 && !g.SB; sb /= 2)
+            if (plain_mt_smem(p, T, qb, sb) <= 227 * 1024) { g.QB = qb; g.SB = sb; }
     if (!g.SB) return g;
     g.n_qtiles = (p->nq + g.QB - 1) / g.QB;
     // about four blocks per SM in total, chunks of at least eight groups
@@ -209,7 +210,7 @@ PlainGeom plain_mt_geometry(const simus_plan *p, int T, int64_t S) {
     len = ((len + g.SB - 1) / g.SB) * g.SB;
     g.chunk_len = std::max<int64_t>(len, g.SB);
     g.n_chunks = (int)((S + g.chunk_len - 1) / g.chunk_len);
-    g.smem = plain_mt_smem(p, T, g.SB);
+    g.smem = plain_mt_smem(p, T, g.QB, g.SB);
     return g;
 }
 
@@ -217,11 +218,15 @@ int launch_plain_mt(const simus_plan *p, const PlainGeom &g, const simus_scat *s
                     const float2 *cw, float2 *part, cudaStream_t st) {
     const bool has_y = sc->y != nullptr;
     const int mode = p->gc.narrow;
-    auto pick = [&](auto hy) {
+    auto pick = [&](auto qb, auto hy) {
+        constexpr int QB = decltype(qb)::value;
         constexpr bool HY = decltype(hy)::value;
-        return mode == 1 ? k_plain_mt<HY, 1> : (mode == 2 ? k_plain_mt<HY, 2> : k_plain_mt<HY, 0>);
+        return mode == 1 ? k_plain_mt<QB, HY, 1> : (mode == 2 ? k_plain_mt<QB, HY, 2> : k_plain_mt<QB, HY, 0>);
     };
-    auto kern = has_y ? pick(std::true_type{}) : pick(std::false_type{});
+    using Q2 = std::integral_constant<int, 2>;
+    using Q4 = std::integral_constant<int, 4>;
+    auto kern = g.QB == 4 ? (has_y ? pick(Q4{}, std::true_type{}) : pick(Q4{}, std::false_type{}))
+                          : (has_y ? pick(Q2{}, std::true_type{}) : pick(Q2{}, std::false_type{}));
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
     if (e != cudaSuccess) return check_cuda(e, "k_plain_mt smem attribute");
     dim3 grid(g.n_qtiles, g.n_chunks);

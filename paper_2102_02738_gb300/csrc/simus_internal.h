@@ -118,9 +118,9 @@ struct PlainGeom { int QB, SB, n_qtiles, n_chunks; int64_t chunk_len; size_t sme
 PlainGeom plain_geometry(const simus_plan *p, int T, int64_t S);
 int launch_plain(const simus_plan *p, const PlainGeom &g, const simus_scat *sc, int T,
                  const float2 *cw, float2 *part, cudaStream_t st);
-// Plain FP32 path for 2 <= T and T N <= 2048: the Green's tile generated once per bin and
-// contracted against every transmit (k_plain_mt.cu); SB = 0 when it does not apply.  Same
-// partial-spectrum layout as launch_plain.
+// Plain FP32 path for T >= 2: the Green's tile generated once per bin and contracted
+// against every transmit (k_plain_mt.cu); SB = 0 when its operands do not fit shared
+// memory (T N beyond ~6,000).  Same partial-spectrum layout as launch_plain.
 PlainGeom plain_mt_geometry(const simus_plan *p, int T, int64_t S);
 int launch_plain_mt(const simus_plan *p, const PlainGeom &g, const simus_scat *sc, int T,
                     const float2 *cw, float2 *part, cudaStream_t st);

@@ -63,7 +63,8 @@ def test_plan_bins_match_oracle(S, oracle):
     dict(elev_focus=float("inf")),
     dict(n_elements=24, n_scat=150, n_tx=7),           # one Green's tile for all transmits
     dict(n_elements=24, n_scat=70, n_tx=7, y_spread=1e-3),
-    dict(n_elements=48, n_scat=40, n_tx=45),           # T N > 2048: per-transmit tiles
+    dict(n_elements=48, n_scat=40, n_tx=45),           # T N = 2160: smaller scatterer groups
+    dict(n_elements=96, n_scat=12, n_tx=70),           # T N = 6720: per-transmit tiles
 ])
 def test_rf_tiny_configs(S, oracle, kw):
     w = ph.tiny(**kw)
