@@ -28,12 +28,6 @@ __device__ __forceinline__ uint32_t h16x2(bool bf16, float lo, float hi) {
     return *reinterpret_cast<const uint32_t *>(&v);
 }
 
-// delta / h from the table of cubic pieces: interval i holds c0..c3 (complex) of
-// c0 + c1 u + c2 u^2 + c3 u^3, u = t - i, t = (x - x0) / dx (two float4 per interval).
-__device__ __forceinline__ float2 cubic_piece(const float4 &lo, const float4 &hi, float u) {
-    return make_float2(fmaf(u, fmaf(u, fmaf(u, hi.z, hi.x), lo.z), lo.x),
-                       fmaf(u, fmaf(u, fmaf(u, hi.w, hi.y), lo.w), lo.y));
-}
 
 // Sub-element sums (Eq. 33) of the Green's terms of elements e0 and e0 + 1 for one
 // scatterer at the NB consecutive bins qA, qA + 1, ...: two independent evaluation chains
