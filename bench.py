@@ -41,9 +41,12 @@ WORKLOADS = {
     "focused-linear-64": ph.focused_linear_64,
     "planewave-linear-128-grad": ph.planewave_linear_128_grad,
     "ragged-batch": ph.ragged_batch,
+    "planewave-linear-128-2d": ph.planewave_linear_128_2d,
+    "pfield-l11-5v": ph.pfield_l11_5v,
 }
 DEFAULT_WORKLOAD = "diverging-convex-128"
 DEFAULT_PATH = {"planewave-linear-128": "plain", "focused-linear-64": "plain",
+                "planewave-linear-128-2d": "plain",
                 "planewave-linear-128-grad": "plain", "diverging-convex-128": "tc_f16"}
 # Per-term instruction budget of the Green's term (FP32 pipe, MUFU) used for the ALU
 # roofline: 85 FP32-pipe instructions + 12 MUFU per (bin, scatterer, sub-element).
@@ -237,7 +240,9 @@ def run_ours(args, rank, ws, local):
     T, N, nt = w.n_tx, w.cfg["n_elements"], info["n_samples"]
     rf = torch.empty((T, N, nt), device=dev)
     terms = metric_terms(w, info)
-    unique_per_launch = terms if path == "plain" else terms / T
+    # Green's terms one launch generates: once per bin for all transmits (tensor-core and
+    # multi-transmit plain kernels), once per transmit only for a single transmit
+    unique_per_launch = terms / T
 
     def step():
         plan.rf(d["delays"], d["apod"], d["x"], None, d["z"], d["rc"], out=rf, stream=stream)
@@ -500,6 +505,109 @@ def run_grad_bench(args, rank, ws, local):
     plan.close()
 
 
+def run_pfield_bench(args, rank, ws, local):
+    """RMS field (Eq. 41-42) of the Fig. 10 L11-5v setup on a 201 x 201 x-z grid, FP32."""
+    import torch
+    from paper_2102_02738_gb300 import build as libbuild
+    libbuild.build()
+    from paper_2102_02738_gb300 import simus
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    peaks, _ = measured_peaks()
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    w = ph.pfield_l11_5v()
+    cfg = w.cfg
+    plan = simus.Plan(cfg, path="plain")
+    xe, ze = ph.element_centres(cfg)
+    r_max = float(np.max(np.hypot(w.x[:, None] - xe[None, :], w.z[:, None] - ze[None, :]))) + cfg["width"]
+    nf = simus.simus_pfield_nfreq(cfg, r_max, float(w.delays.max()))
+    host = {k: np.ascontiguousarray(getattr(w, k)) for k in ("delays", "apod", "x", "z")}
+    d = {k: torch.from_numpy(v).to(dev) for k, v in host.items()}
+    npts = w.x.size
+    out = torch.empty((w.n_tx, npts), device=dev)
+    M = plan.info["n_sub"] * cfg["n_elements"]
+    terms = float(npts) * nf * M * w.n_tx
+
+    def step():
+        plan.pfield(d["delays"], d["apod"], d["x"], None, d["z"], nf, out=out, stream=stream)
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    simus.simus_plan_set_profiling(plan.handle, True)
+    clocks = ClockSampler(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    stage_ms = []
+    launches0 = simus.simus_kernel_launches()
+    clocks.start()
+    time.sleep(0.5)
+    barrier(ws)
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+        stage_ms.append(simus.simus_plan_get_timings(plan.handle))
+    torch.cuda.synchronize()
+    barrier(ws)
+    launches = simus.simus_kernel_launches() - launches0
+    clk = clocks.stop()
+    ms_per_step = allreduce_max(sum(a.elapsed_time(b) for a, b in ev), ws) / args.steps
+    kern_ms = statistics.mean(s["pfield"] for s in stage_ms)
+    peak = alu_peak_terms(n_sm, float(peaks.get("sm_max_mhz", 2070.0)))
+    achieved = terms / (kern_ms / 1e3)
+    # end to end: grid coordinates in, field out, through pinned host buffers
+    pin = {k: torch.from_numpy(host[k]).pin_memory() for k in ("x", "z")}
+    out_h = torch.empty((w.n_tx, npts), dtype=torch.float32).pin_memory()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_ms = 0.0
+    n_e2e = max(1, min(args.steps, 5))
+    for i in range(n_e2e):
+        flush.fill_(float(i))
+        e0.record(stream)
+        for k in pin:
+            d[k].copy_(pin[k], non_blocking=True)
+        step()
+        out_h.copy_(out, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms += e0.elapsed_time(e1)
+    e2e_ms = allreduce_max(e2e_ms, ws) / n_e2e
+    line = {"metric": METRIC.replace("scatterer", "field point"), "value": terms * ws / (ms_per_step / 1e3),
+            "unit": "terms/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "pfield-l11-5v", "points": npts, "frequencies": nf,
+                       "sub_elements_total": M, "transmits": w.n_tx, "terms_per_step": terms,
+                       "l2": "flushed between timed steps (256 MB write)"},
+            "roofline": {"bound": "alu", "kernel": "k_pfield", "achieved": achieved / 1e9,
+                         "peak": peak / 1e9, "unit": "Gterm/s", "frac": achieved / peak,
+                         "traffic": None, "kernel_ms": kern_ms},
+            "e2e": {"value": terms * ws / (e2e_ms / 1e3), "unit": "terms/s",
+                    "h2d_bytes_per_step": sum(v.numel() * 4 for v in pin.values()),
+                    "d2h_bytes_per_step": out_h.numel() * 4},
+            "gpu_launches": launches, "clocks": clk}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        from oracle import oracle as orc
+        sel = np.linspace(0, npts - 1, 60).astype(np.int64)
+        t0 = time.time()
+        ref = orc.pfield(cfg, w.delays, w.apod, w.x[sel], None, w.z[sel], nf)
+        dt = time.time() - t0
+        got = out.cpu().numpy()[:, sel]
+        line["cpu_baseline"] = {"value": float(sel.size) * nf * M * w.n_tx / dt, "unit": "terms/s",
+                                "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+                                "sample": f"{sel.size} of {npts} grid points, all {nf} frequencies, FP64, {dt:.1f} s"}
+        line["accuracy"] = {"rel_l2_vs_fp64_oracle": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+                            "compared": f"RMS pressure at the {sel.size} sampled points", "tolerance": 1e-5}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -523,6 +631,8 @@ def main():
         run_batch_bench(args, rank, ws, local)
     elif args.workload == "planewave-linear-128-grad":
         run_grad_bench(args, rank, ws, local)
+    elif args.workload == "pfield-l11-5v":
+        run_pfield_bench(args, rank, ws, local)
     else:
         run_ours(args, rank, ws, local)
     if ws > 1:

@@ -41,12 +41,14 @@ __global__ void k_pfield_weights(int T, int N, int nf, int j0, double df,
     }
 }
 
-template <bool HAS_Y, bool NARROW>
+// TAB: delta/h at Y = 0 from the plan's table of cubic pieces (read-only cache; relative
+// error <= 2.3e-6), evaluated directly within ~2 mm of a sub-element.
+template <bool HAS_Y, bool NARROW, bool TAB>
 __global__ void __launch_bounds__(kPThreads, 2)
 k_pfield(const GreenConst gc, const SubElem *__restrict__ sub_g, const float *__restrict__ xg,
          const float *__restrict__ yg, const float *__restrict__ zg, int64_t npts, int nf, int j0,
          const float2 *__restrict__ wt, const float *__restrict__ ptx2, float dw,
-         float *__restrict__ prms) {
+         float *__restrict__ prms, const float4 *__restrict__ dtab) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int N = gc.N, nu = gc.nu, M = gc.M;
     const int tid = threadIdx.x, t = blockIdx.y;
@@ -74,11 +76,23 @@ k_pfield(const GreenConst gc, const SubElem *__restrict__ sub_g, const float *__
             const int e = n / nu;
             PairSetup P = pair_setup<HAS_Y>(gc, sub[n], xs, ys, zs, q0);
             PhaseRun R = phase_run(P, q0);
+            const float kt = TAB ? P.kap * gc.tab_inv_dx : 0.0f;
+            const float t0 = TAB ? gc.tab_x0 * gc.tab_inv_dx : 0.0f;
 #pragma unroll
             for (int j = 0; j < kPQB; ++j) {
                 const float q = q0 + (float)j;
                 const float m = sinc_f<NARROW>(q * P.xb);
-                const float2 d = delta_f<HAS_Y>(gc, P, q);
+                float2 d;
+                if (TAB) {
+                    const float tt = fmaf(q, kt, -t0);
+                    const float fl = floorf(fminf(fmaxf(tt, 0.0f), (float)gc.tab_n - 0.5f));
+                    const int ii = (int)fl;
+                    const float u = tt - fl;
+                    d = cubic_piece(__ldg(dtab + 2 * ii), __ldg(dtab + 2 * ii + 1), u);
+                    if (!(u >= 0.0f && u <= 1.0f)) d = delta_f<false>(gc, P, q);
+                } else {
+                    d = delta_f<HAS_Y>(gc, P, q);
+                }
                 const float er = R.zr * m, ei = R.zi * m;
                 const float gr = er * d.x - ei * d.y, gi = er * d.y + ei * d.x;
                 const float2 w = wtt[j * N + e];
@@ -111,12 +125,15 @@ int launch_pfield(const simus_plan *p, const GreenConst &gc, const simus_tx *tx,
     }
     const size_t smem = sizeof(SubElem) * p->M + sizeof(float2) * (size_t)kPQB * p->N;
     const bool has_y = y != nullptr, narrow = gc.narrow == 1;
-    auto kern = has_y ? (narrow ? k_pfield<true, true> : k_pfield<true, false>)
-                      : (narrow ? k_pfield<false, true> : k_pfield<false, false>);
+    const bool tab = !has_y && p->d_dtab && gc.tab_n > 0;
+    auto kern = has_y ? (narrow ? k_pfield<true, true, false> : k_pfield<true, false, false>)
+              : tab   ? (narrow ? k_pfield<false, true, true> : k_pfield<false, false, true>)
+                      : (narrow ? k_pfield<false, true, false> : k_pfield<false, false, false>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return check_cuda(e, "k_pfield smem attribute");
     dim3 grid((unsigned)((npts + kPThreads - 1) / kPThreads), T);
-    kern<<<grid, kPThreads, smem, st>>>(gc, p->d_sub, x, y, z, npts, nf, j0, wt, ptx2, dw, prms);
+    kern<<<grid, kPThreads, smem, st>>>(gc, p->d_sub, x, y, z, npts, nf, j0, wt, ptx2, dw, prms,
+                                        p->d_dtab);
     count_launches(1);
     return check_cuda(cudaGetLastError(), "k_pfield launch");
 }

@@ -812,6 +812,11 @@ int simus_pfield(simus_plan *plan, const simus_tx *tx, int64_t n_pts, const floa
     if (j_lo < 0) return fail(SIMUS_ERR_ARG, "empty transmit spectrum");
     const int nf = j_hi - j_lo + 1;
     GreenConst gc = green_const(plan->probe, plan->medium, plan->N, plan->nu, df, j_hi + 0.5);
+    if (plan->d_dtab && plan->delta_table) {   // the delta table's abscissa is physical (x), not a bin index
+        gc.tab_n = plan->gc.tab_n;
+        gc.tab_x0 = plan->gc.tab_x0;
+        gc.tab_inv_dx = plan->gc.tab_inv_dx;
+    }
     const int T = tx->n_tx;
     const size_t wt_b = align256(sizeof(float2) * (size_t)T * nf * plan->N);
     const size_t p2_b = align256(sizeof(float) * nf);

@@ -202,6 +202,31 @@ def planewave_linear_128(seed=1002, n_scat=20000, with_points=True):
                    plane_wave_delays(probe, med["c"], [0.0]), x, z, rc)
 
 
+def planewave_linear_128_2d(seed=1002, n_scat=20000, with_points=True):
+    """The planewave-linear-128 problem in the 2-D x-z model of Section V (Eq. 36-38)."""
+    w = planewave_linear_128(seed, n_scat, with_points)
+    w.cfg["two_d"] = 1
+    w.name = w.name.replace("planewave-linear-128", "planewave-linear-128-2d")
+    return w
+
+
+def pfield_l11_5v(nx=201, nz=201, tilt_deg=10.0):
+    """Fig. 10 setup for the RMS field (Eq. 41-42): 128-element 7.6 MHz linear array,
+    pitch 0.27 mm, kerf 30 um, 77 % bandwidth, elevation focus 18 mm, one plane wave tilted
+    by tilt_deg; an nx x nz grid over x in [-20, 20] mm, z in [0.5, 40] mm at y = 0."""
+    probe = linear_probe(128, 7.6e6, 0.27e-3, 0.03e-3, elev_focus=0.018, frac_bw=0.77)
+    med = medium(7.6e6)
+    X, Z = np.meshgrid(np.linspace(-20e-3, 20e-3, nx), np.linspace(0.5e-3, 40e-3, nz))
+    delays = plane_wave_delays(probe, med["c"], [math.radians(tilt_deg)])
+    cfg = dict(probe)
+    cfg.update(med)
+    cfg["n_samples"] = 64   # unused by the field; a plan needs one
+    return Workload("pfield-l11-5v", cfg, np.asarray(delays, np.float32),
+                    np.ones_like(delays, dtype=np.float32), X.ravel().astype(np.float32), None,
+                    Z.ravel().astype(np.float32), np.zeros(X.size, np.float32),
+                    dict(nx=nx, nz=nz))
+
+
 def diverging_convex_128(seed=1003, n_scat=100000, n_tx=31):
     """128-element 3 MHz convex array (R = 60 mm, pitch 0.5 mm, nu = 2), 31 diverging
     waves over +-20 degrees, speckle uniform in area in a 60-degree sector to 120 mm."""
