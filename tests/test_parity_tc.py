@@ -50,6 +50,12 @@ def rel_l2(a, b):
     dict(n_elements=13, n_sub=3, n_scat=150, n_tx=3),        # N not a multiple of 8
     dict(convex=True, n_elements=24, n_scat=200, n_tx=9),
     dict(y_spread=1e-3, n_scat=130),
+    # wide arrays: 96-112 KB tiles leave room for one shared-memory tile buffer, so the
+    # later bins of a pass wait in tensor-memory stash slots
+    dict(n_elements=176, n_sub=1, n_scat=140, n_tx=3),      # two buffers, receive in halves
+    dict(n_elements=200, n_sub=1, n_scat=140, n_tx=3),      # one buffer, two stash slots
+    dict(n_elements=256, n_sub=1, n_scat=140, n_tx=2),      # one buffer, one stash slot
+    dict(n_elements=200, n_sub=1, n_scat=60, n_tx=21),      # large T x N: one bin per pass
 ])
 def test_tc_f16_rf_tiny(S, oracle, kw):
     w = ph.tiny(**kw)
