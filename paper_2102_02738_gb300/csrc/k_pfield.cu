@@ -6,8 +6,9 @@
 // The midpoint frequencies are f_j = (j + 1/2) df with df = 2 fc / N_f, so the Green's
 // machinery runs with half-integer "bin indices" q = j + 1/2 and that df.
 //
-// Thread per field point; frequencies in runs of QB (phase recurrence over the run),
-// all sub-elements accumulated per run, then |.|^2 weighted and summed.  Frequencies
+// Thread per field point and chunk of frequencies; frequencies in runs of QB (phase
+// recurrence over the run), all sub-elements accumulated per run, then |.|^2 weighted and
+// summed; with several chunks their partial sums are added in a fixed order afterwards.  Frequencies
 // whose |P_Tx|^2 is below 1e-12 of its maximum are skipped (their share of the sum is
 // below 1e-12 N_f relative).
 #include <algorithm>
@@ -48,7 +49,8 @@ __global__ void __launch_bounds__(kPThreads, 2)
 k_pfield(const GreenConst gc, const SubElem *__restrict__ sub_g, const float *__restrict__ xg,
          const float *__restrict__ yg, const float *__restrict__ zg, int64_t npts, int nf, int j0,
          const float2 *__restrict__ wt, const float *__restrict__ ptx2, float dw,
-         float *__restrict__ prms, const float4 *__restrict__ dtab) {
+         float *__restrict__ prms, const float4 *__restrict__ dtab, int fchunk,
+         float *__restrict__ ppart) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int N = gc.N, nu = gc.nu, M = gc.M;
     const int tid = threadIdx.x, t = blockIdx.y;
@@ -60,12 +62,14 @@ k_pfield(const GreenConst gc, const SubElem *__restrict__ sub_g, const float *__
     const bool live = i < npts;
     const float xs = live ? xg[i] : 0.f, zs = live ? zg[i] : 1.f;
     const float ys = (HAS_Y && live) ? yg[i] : 0.f;
+    // frequency chunk blockIdx.z: [jbeg, jend) of the nf midpoints (a multiple of kPQB)
+    const int jbeg = min(nf, (int)blockIdx.z * fchunk), jend = min(nf, jbeg + fchunk);
     float power = 0.f;
-    for (int jb = 0; jb < nf; jb += kPQB) {
+    for (int jb = jbeg; jb < jend; jb += kPQB) {
         __syncthreads();
         for (int k = tid; k < kPQB * N; k += kPThreads) {
             const int jj = k / N, e = k - jj * N;
-            wtt[k] = jb + jj < nf ? wt[((size_t)t * nf + jb + jj) * N + e] : make_float2(0.f, 0.f);
+            wtt[k] = jb + jj < jend ? wt[((size_t)t * nf + jb + jj) * N + e] : make_float2(0.f, 0.f);
         }
         __syncthreads();
         const float q0 = (float)(j0 + jb) + 0.5f;
@@ -105,14 +109,44 @@ k_pfield(const GreenConst gc, const SubElem *__restrict__ sub_g, const float *__
         }
 #pragma unroll
         for (int j = 0; j < kPQB; ++j)
-            if (jb + j < nf) power = fmaf(ptx2[jb + j], ar[j] * ar[j] + ai[j] * ai[j], power);
+            if (jb + j < jend) power = fmaf(ptx2[jb + j], ar[j] * ar[j] + ai[j] * ai[j], power);
     }
-    if (live) prms[(size_t)t * npts + i] = sqrtf(dw * power);
+    if (!live) return;
+    if (ppart) ppart[((size_t)blockIdx.z * gridDim.y + t) * npts + i] = power;   // partial sum
+    else prms[(size_t)t * npts + i] = sqrtf(dw * power);
+}
+
+// prms[t][i] = sqrt(dw sum_c ppart[c][t][i]), chunks summed in a fixed order.
+__global__ void k_pfield_finish(const float *__restrict__ ppart, int n_chunks, int64_t n,
+                                float dw, float *__restrict__ prms) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        float a = 0.f;
+        for (int c = 0; c < n_chunks; ++c) a += ppart[(size_t)c * n + i];
+        prms[i] = sqrtf(dw * a);
+    }
+}
+
+// Frequency chunks (a multiple of kPQB each) until the grid fills the GPU a few times
+// over: n_fc chunks of fchunk midpoints.
+static void pfield_split(const simus_plan *p, int T, int64_t npts, int nf, int &n_fc, int &fchunk) {
+    const int64_t pblocks = ((npts + kPThreads - 1) / kPThreads) * T;
+    n_fc = 1;
+    while (n_fc < 64 && pblocks * n_fc < (int64_t)p->num_sms * 4 && (nf + 2 * n_fc - 1) / (2 * n_fc) >= 2 * kPQB)
+        n_fc *= 2;
+    fchunk = ((nf + n_fc - 1) / n_fc + kPQB - 1) / kPQB * kPQB;
+    n_fc = (nf + fchunk - 1) / fchunk;
+}
+
+int pfield_fchunks(const simus_plan *p, int T, int64_t npts, int nf) {
+    int n_fc, fchunk;
+    pfield_split(p, T, npts, nf, n_fc, fchunk);
+    return n_fc;
 }
 
 int launch_pfield(const simus_plan *p, const GreenConst &gc, const simus_tx *tx, int64_t npts,
                   const float *x, const float *y, const float *z, int nf, int j0, float2 *wt,
-                  const float *ptx2, float dw, float *prms, cudaStream_t st) {
+                  const float *ptx2, float dw, float *prms, float *ppart, cudaStream_t st) {
     const int T = tx->n_tx;
     {
         int64_t total = (int64_t)T * nf * p->N;
@@ -131,11 +165,19 @@ int launch_pfield(const simus_plan *p, const GreenConst &gc, const simus_tx *tx,
                       : (narrow ? k_pfield<false, true, false> : k_pfield<false, false, false>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return check_cuda(e, "k_pfield smem attribute");
-    dim3 grid((unsigned)((npts + kPThreads - 1) / kPThreads), T);
+    int n_fc, fchunk;
+    pfield_split(p, T, npts, nf, n_fc, fchunk);
+    dim3 grid((unsigned)((npts + kPThreads - 1) / kPThreads), T, n_fc);
     kern<<<grid, kPThreads, smem, st>>>(gc, p->d_sub, x, y, z, npts, nf, j0, wt, ptx2, dw, prms,
-                                        p->d_dtab);
+                                        p->d_dtab, fchunk, n_fc > 1 ? ppart : nullptr);
     count_launches(1);
-    return check_cuda(cudaGetLastError(), "k_pfield launch");
+    int rc = check_cuda(cudaGetLastError(), "k_pfield launch");
+    if (rc || n_fc == 1) return rc;
+    const int64_t n = (int64_t)T * npts;
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)p->num_sms * 8);
+    k_pfield_finish<<<blocks, 256, 0, st>>>(ppart, n_fc, n, dw, prms);
+    count_launches(1);
+    return check_cuda(cudaGetLastError(), "k_pfield_finish launch");
 }
 
 }  // namespace simus

@@ -820,15 +820,18 @@ int simus_pfield(simus_plan *plan, const simus_tx *tx, int64_t n_pts, const floa
     const int T = tx->n_tx;
     const size_t wt_b = align256(sizeof(float2) * (size_t)T * nf * plan->N);
     const size_t p2_b = align256(sizeof(float) * nf);
+    const int n_fc = pfield_fchunks(plan, T, n_pts, nf);
+    const size_t pp_b = n_fc > 1 ? align256(sizeof(float) * (size_t)n_fc * T * n_pts) : 0;
     void *ws;
-    if ((rc = workspace(plan, wt_b + p2_b, &ws))) return rc;
+    if ((rc = workspace(plan, wt_b + p2_b + pp_b, &ws))) return rc;
     float2 *wt = reinterpret_cast<float2 *>(ws);
     float *d_p2 = reinterpret_cast<float *>(reinterpret_cast<char *>(ws) + wt_b);
+    float *ppart = n_fc > 1 ? reinterpret_cast<float *>(reinterpret_cast<char *>(ws) + wt_b + p2_b) : nullptr;
     if ((rc = check_cuda(cudaMemcpyAsync(d_p2, p2.data() + j_lo, sizeof(float) * nf,
                                          cudaMemcpyHostToDevice, st), "upload |P_Tx|^2")))
         return rc;
     stage_begin(plan, 4, st);
-    rc = launch_pfield(plan, gc, tx, n_pts, x, y, z, nf, j_lo, wt, d_p2, (float)dw, prms, st);
+    rc = launch_pfield(plan, gc, tx, n_pts, x, y, z, nf, j_lo, wt, d_p2, (float)dw, prms, ppart, st);
     stage_end(plan, 4, st);
     return rc;
 }
