@@ -336,7 +336,7 @@ GradGeom grad_geometry(const simus_plan *p, int T, int64_t S) {
              + sizeof(float2) * (size_t)kGQB * SB * T + sizeof(float) * 3 * kGQB * SB * T;
     };
     g.SB = smem_for(kGSBMax) <= 227 * 1024 ? kGSBMax : 8;
-    int64_t want = (int64_t)p->num_sms * 4;
+    int64_t want = (int64_t)p->num_sms * 8;
     int64_t chunks = std::max<int64_t>(1, (want + g.n_qtiles - 1) / g.n_qtiles);
     chunks = std::min<int64_t>(chunks, std::max<int64_t>(1, S / (g.SB * 16)));
     int64_t len = (S + chunks - 1) / chunks;

@@ -217,8 +217,8 @@ PlainGeom plain_mt_geometry(const simus_plan *p, int T, int64_t S) {
             if (plain_mt_smem(p, T, qb, sb) <= 227 * 1024) { g.QB = qb; g.SB = sb; }
     if (!g.SB) return g;
     g.n_qtiles = (p->nq + g.QB - 1) / g.QB;
-    // about four blocks per SM in total, chunks of at least eight groups
-    const int64_t want = (int64_t)p->num_sms * 4;
+    // about eight blocks per SM in total (a short last wave), chunks of at least eight groups
+    const int64_t want = (int64_t)p->num_sms * 8;
     int64_t chunks = std::max<int64_t>(1, (want + g.n_qtiles - 1) / g.n_qtiles);
     chunks = std::min<int64_t>(chunks, std::max<int64_t>(1, S / ((int64_t)g.SB * 8)));
     int64_t len = (S + chunks - 1) / chunks;
