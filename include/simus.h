@@ -199,6 +199,16 @@ int simus_batch_rf(int32_t n_sims, simus_plan *const *plans, const simus_tx *tx,
  * SIMUS_ERR_CUDA for an asynchronous CUDA error, else SIMUS_OK. */
 int simus_plan_check(simus_plan *plan);
 
+/* Failure-detection self-test (a diagnostic; the paper has no counterpart).  Enqueues one
+ * block that waits, with the same bounded mbarrier wait the tensor-core kernel uses, for a
+ * barrier phase that nothing ever completes; the wait gives up after max_polls polls
+ * (1 <= max_polls <= 2^24; each poll may suspend the thread for a short, hardware-defined
+ * time) and records SIMUS_ERR_TIMEOUT in the plan's error flag, exactly as a stalled
+ * tensor-core work item would.  The next simus_plan_check then returns SIMUS_ERR_TIMEOUT
+ * (and clears the flag) and the device stays usable.  Returns SIMUS_ERR_ARG for a NULL
+ * plan or max_polls out of range, SIMUS_ERR_CUDA if the launch fails, else SIMUS_OK. */
+int simus_plan_selftest_timeout(simus_plan *plan, int32_t max_polls, void *stream);
+
 /* Per-stage timing of the calls made on a plan (tracing).  With profiling enabled,
  * each entry point records CUDA events around its kernels on the call's stream;
  * simus_plan_get_timings waits for them and writes the durations in milliseconds of

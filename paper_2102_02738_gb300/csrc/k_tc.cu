@@ -155,6 +155,25 @@ TcShape tc_shape(const simus_plan *p, int T, int64_t S, double work_share, int i
 }
 
 
+// One block waits for the second phase of an mbarrier that expects one arrival that
+// never comes; the bounded wait gives up and the error flag is set as in k_tc_rf.
+__global__ void k_selftest_timeout(int max_polls, int *err) {
+    __shared__ uint64_t bar;
+    const uint32_t mbar = tc::smem_u32(&bar);
+    if (threadIdx.x == 0) {
+        tc::mbar_init(mbar, 1);
+        tc::fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !tc::mbar_wait_bounded(mbar, 0, max_polls)) atomicExch(err, SIMUS_ERR_TIMEOUT);
+}
+
+int launch_selftest_timeout(int max_polls, int *err, cudaStream_t st) {
+    k_selftest_timeout<<<1, 32, 0, st>>>(max_polls, err);
+    count_launches(1);
+    return check_cuda(cudaGetLastError(), "k_selftest_timeout launch");
+}
+
 int launch_tc_units(const TcUnit *h_units, const TcUnit *d_units, int n_units, int64_t n_items,
                     size_t smem, bool bf16, bool has_y, int sinc_mode, bool linear, int num_sms,
                     int *counter, int *err, cudaStream_t st) {

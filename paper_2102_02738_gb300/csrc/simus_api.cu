@@ -462,6 +462,14 @@ int simus_plan_check(simus_plan *plan) {
     return SIMUS_OK;
 }
 
+int simus_plan_selftest_timeout(simus_plan *plan, int32_t max_polls, void *stream) {
+    if (!plan) return fail(SIMUS_ERR_ARG, "plan must not be NULL");
+    if (max_polls < 1 || max_polls > (1 << 24)) return fail(SIMUS_ERR_ARG, "max_polls outside [1, 2^24]");
+    int rc = use_plan_device(plan);
+    if (rc) return rc;
+    return launch_selftest_timeout(max_polls, plan->d_err, reinterpret_cast<cudaStream_t>(stream));
+}
+
 int simus_plan_set_profiling(simus_plan *plan, int32_t enable) {
     if (!plan) return fail(SIMUS_ERR_ARG, "plan must not be NULL");
     int rc = use_plan_device(plan);

@@ -176,6 +176,9 @@ int launch_tc_units(const TcUnit *h_units, const TcUnit *d_units, int n_units, i
                     size_t smem, bool bf16, bool has_y, int sinc_mode, bool linear, int num_sms,
                     int *counter, int *err, cudaStream_t st);
 
+// Failure-detection self-test: a bounded wait on a barrier phase nothing completes.
+int launch_selftest_timeout(int max_polls, int *err, cudaStream_t st);
+
 // Adjoint (gradient) path, FP32.
 struct GradGeom {
     bool ok;             // T * N <= 2048 and the shared-memory tiles fit

@@ -97,6 +97,7 @@ def _load():
     L.simus_kernel_launches.restype = i64
     L.simus_kernel_launches.argtypes = []
     L.simus_plan_check.argtypes = [vp]
+    L.simus_plan_selftest_timeout.argtypes = [vp, i32, vp]
     L.simus_rf_noalloc.argtypes = [C.POINTER(Probe), C.POINTER(Medium), i32, C.POINTER(Tx),
                                    C.POINTER(Scat), vp, vp]
     return L
