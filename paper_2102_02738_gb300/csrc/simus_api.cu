@@ -395,6 +395,7 @@ int32_t simus_pfield_nfreq(const simus_probe *probe, const simus_medium *medium,
 
 int simus_plan_create(const simus_probe *probe, const simus_medium *medium, int32_t n_samples,
                       int32_t path, simus_plan **out) {
+    NvtxScope nvtx_scope("simus_plan_create");
     if (!out) return fail(SIMUS_ERR_ARG, "out must not be NULL");
     *out = nullptr;
     simus_plan *p = new simus_plan();
@@ -750,6 +751,7 @@ extern "C" {
 
 int simus_rf_spectrum(simus_plan *plan, const simus_tx *tx, const simus_scat *scat, float *spec,
                       void *stream) {
+    NvtxScope nvtx_scope("simus_rf_spectrum");
     CaptureScope capture_scope(stream);
     if (!plan) return fail(SIMUS_ERR_ARG, "plan must not be NULL");
     for (bool &u : plan->stage_used) u = false;
@@ -769,6 +771,7 @@ int simus_rf_spectrum(simus_plan *plan, const simus_tx *tx, const simus_scat *sc
 
 int simus_rf(simus_plan *plan, const simus_tx *tx, const simus_scat *scat, float *rf,
              void *stream) {
+    NvtxScope nvtx_scope("simus_rf");
     CaptureScope capture_scope(stream);
     if (!plan) return fail(SIMUS_ERR_ARG, "plan must not be NULL");
     for (bool &u : plan->stage_used) u = false;
@@ -788,6 +791,7 @@ int simus_rf(simus_plan *plan, const simus_tx *tx, const simus_scat *scat, float
 
 int simus_pfield(simus_plan *plan, const simus_tx *tx, int64_t n_pts, const float *x,
                  const float *y, const float *z, int32_t n_freq, float *prms, void *stream) {
+    NvtxScope nvtx_scope("simus_pfield");
     CaptureScope capture_scope(stream);
     if (!plan) return fail(SIMUS_ERR_ARG, "plan must not be NULL");
     for (bool &u : plan->stage_used) u = false;
@@ -846,6 +850,7 @@ int simus_pfield(simus_plan *plan, const simus_tx *tx, int64_t n_pts, const floa
 
 int simus_rf_grad(simus_plan *plan, const simus_tx *tx, const simus_scat *scat, const float *drf,
                   float *g_rc, float *g_x, float *g_z, float *g_delays, void *stream) {
+    NvtxScope nvtx_scope("simus_rf_grad");
     CaptureScope capture_scope(stream);
     if (!plan) return fail(SIMUS_ERR_ARG, "plan must not be NULL");
     for (bool &u : plan->stage_used) u = false;
@@ -896,6 +901,7 @@ int simus_rf_grad(simus_plan *plan, const simus_tx *tx, const simus_scat *scat, 
 
 int simus_batch_rf(int32_t n_sims, simus_plan *const *plans, const simus_tx *tx,
                    const simus_scat *scat, float *const *rf, void *stream) {
+    NvtxScope nvtx_scope("simus_batch_rf");
     CaptureScope capture_scope(stream);
     if (n_sims < 0 || (n_sims > 0 && (!plans || !tx || !scat || !rf)))
         return fail(SIMUS_ERR_ARG, "invalid batch arguments");

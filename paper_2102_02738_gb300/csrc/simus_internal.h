@@ -5,6 +5,7 @@
 #include <cstdint>
 #include <vector>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/simus.h"
 
@@ -102,8 +103,15 @@ int launch_pfield(const simus_plan *p, const GreenConst &gc, const simus_tx *tx,
                   const float *x, const float *y, const float *z, int nf, int j0, float2 *wt,
                   const float *ptx2, float dw, float *prms, float *ppart, cudaStream_t st);
 
-// Tracing: events around a stage (no-ops unless profiling is enabled) and the
+// Tracing: an NVTX range around each entry point (visible to Nsight tools, free
+// otherwise), events around a stage (no-ops unless profiling is enabled) and the
 // process-wide launch counter.
+struct NvtxScope {
+    explicit NvtxScope(const char *name) { nvtxRangePushA(name); }
+    ~NvtxScope() { nvtxRangePop(); }
+    NvtxScope(const NvtxScope &) = delete;
+    NvtxScope &operator=(const NvtxScope &) = delete;
+};
 void stage_begin(simus_plan *plan, int stage, cudaStream_t st);
 void stage_end(simus_plan *plan, int stage, cudaStream_t st);
 void count_launches(int n);
