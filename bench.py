@@ -42,11 +42,12 @@ WORKLOADS = {
     "planewave-linear-128-grad": ph.planewave_linear_128_grad,
     "ragged-batch": ph.ragged_batch,
     "planewave-linear-128-2d": ph.planewave_linear_128_2d,
+    "diverging-convex-128-3d": ph.diverging_convex_128_3d,
     "pfield-l11-5v": ph.pfield_l11_5v,
 }
 DEFAULT_WORKLOAD = "diverging-convex-128"
 DEFAULT_PATH = {"planewave-linear-128": "plain", "focused-linear-64": "plain",
-                "planewave-linear-128-2d": "plain",
+                "planewave-linear-128-2d": "plain", "diverging-convex-128-3d": "tc_f16",
                 "planewave-linear-128-grad": "plain", "diverging-convex-128": "tc_f16"}
 # Per-term instruction budget of the Green's term (FP32 pipe, MUFU) used for the ALU
 # roofline: 85 FP32-pipe instructions + 12 MUFU per (bin, scatterer, sub-element).
@@ -233,7 +234,8 @@ def run_ours(args, rank, ws, local):
 
     w = WORKLOADS[args.workload](**({"n_scat": args.n_scat} if args.n_scat else {}))
     path = args.path or DEFAULT_PATH[args.workload]
-    host = {k: np.ascontiguousarray(getattr(w, k)) for k in ("delays", "apod", "x", "z", "rc")}
+    keys = ("delays", "apod", "x", "z", "rc") + (("y",) if w.y is not None else ())
+    host = {k: np.ascontiguousarray(getattr(w, k)) for k in keys}
     d = {k: torch.from_numpy(v).to(dev) for k, v in host.items()}
     plan = simus.Plan(w.cfg, path=path)
     info = plan.info
@@ -245,7 +247,7 @@ def run_ours(args, rank, ws, local):
     unique_per_launch = terms / T
 
     def step():
-        plan.rf(d["delays"], d["apod"], d["x"], None, d["z"], d["rc"], out=rf, stream=stream)
+        plan.rf(d["delays"], d["apod"], d["x"], d.get("y"), d["z"], d["rc"], out=rf, stream=stream)
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2
     for _ in range(max(args.warmup, 0)):
@@ -311,12 +313,12 @@ def run_ours(args, rank, ws, local):
     if path != "plain" and not args.no_plain_compare:
         pplan = simus.Plan(w.cfg, path="plain")
         simus.simus_plan_set_profiling(pplan.handle, True)
-        pplan.rf(d["delays"], d["apod"], d["x"], None, d["z"], d["rc"], out=rf, stream=stream)
+        pplan.rf(d["delays"], d["apod"], d["x"], d.get("y"), d["z"], d["rc"], out=rf, stream=stream)
         torch.cuda.synchronize()
         flush.fill_(0.5)
         p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         p0.record(stream)
-        pplan.rf(d["delays"], d["apod"], d["x"], None, d["z"], d["rc"], out=rf, stream=stream)
+        pplan.rf(d["delays"], d["apod"], d["x"], d.get("y"), d["z"], d["rc"], out=rf, stream=stream)
         p1.record(stream)
         p1.synchronize()
         pms = p0.elapsed_time(p1)
@@ -332,7 +334,7 @@ def run_ours(args, rank, ws, local):
         cpu = {"value": v, "unit": "terms/s", "cores": cores, "kind": "oracle",
                "sample": f"RF spectrum at {k} of {info['n_bins']} kept bins, all "
                          f"{w.n_scat} scatterers and {T} transmits, FP64, {dt:.1f} s"}
-        spec = plan.rf_spectrum(d["delays"], d["apod"], d["x"], None, d["z"], d["rc"])
+        spec = plan.rf_spectrum(d["delays"], d["apod"], d["x"], d.get("y"), d["z"], d["rc"])
         Xg = spec.cpu().numpy()[..., qs - info["q_lo"]]
         accuracy = {"rel_l2_vs_fp64_oracle": float(np.linalg.norm(Xg - Xo) / np.linalg.norm(Xo)),
                     "compared": f"RF spectra X_q(e,t) at the {k} sampled bins, every element "

@@ -281,7 +281,7 @@ k_tc_rf(const TcUnit *__restrict__ units, int n_units, int64_t n_items, int *cou
             __syncthreads();
         }
         const GreenConst gc = U.gc;   // register copy: the per-pair setup reads it often
-        const int N = gc.N, nu = gc.nu, M = gc.M, nq = gc.nq;
+        const int N = gc.N, M = gc.M, nq = gc.nq;
         const int Np = U.Np, nN = U.nN, TG = U.TG, QB = U.QB, mh = U.mh, pair = U.pair;
         const int G = U.G, T = U.T, nbuf = U.nbuf;
         const int K1 = 2 * Np;

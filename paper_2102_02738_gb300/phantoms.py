@@ -210,6 +210,17 @@ def planewave_linear_128_2d(seed=1002, n_scat=20000, with_points=True):
     return w
 
 
+def diverging_convex_128_3d(seed=1003, n_scat=100000, n_tx=31, y_half=2.5e-3):
+    """The diverging-convex-128 problem with a 3-D scatterer cloud: elevations uniform in
+    [-y_half, y_half] (the element height is 5 mm), so that delta carries the Eq. 14
+    exponent (beta, gamma != 0; Section VIII's 3-D case)."""
+    w = diverging_convex_128(seed, n_scat, n_tx)
+    w.y = (y_half * (2.0 * uniform(seed, 9, w.n_scat) - 1.0)).astype(np.float32)
+    w.cfg["n_samples"] = rf_length(w.cfg, w.x, w.z, w.delays, w.y)
+    w.name = w.name.replace("diverging-convex-128", "diverging-convex-128-3d")
+    return w
+
+
 def pfield_l11_5v(nx=201, nz=201, tilt_deg=10.0):
     """Fig. 10 setup for the RMS field (Eq. 41-42): 128-element 7.6 MHz linear array,
     pitch 0.27 mm, kerf 30 um, 77 % bandwidth, elevation focus 18 mm, one plane wave tilted
