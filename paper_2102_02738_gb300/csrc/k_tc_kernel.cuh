@@ -389,10 +389,16 @@ k_tc_rf(const TcUnit *__restrict__ units, int n_units, int64_t n_items, int *cou
                         } else {
                             b1_inflight = false;
                             tc::fence_after_sync();
-                            for (int j = 0; j < K1 / 16; ++j) {
-                                uint64_t ad = tc::smem_desc(abase + 256 * j, 128, 16 * K1);
-                                uint64_t bd = tc::smem_desc(b1s + 256 * j, 128, 16 * K1);
-                                tc::mma_f16(tmem, ad, bd, idesc1, j > 0);
+                            // K1 / 16 <= 32 steps of 256 bytes (16 in the descriptors'
+                            // address field); unrolled so that the issuing thread does not
+                            // recompute descriptors between MMAs
+                            const uint64_t ad0 = tc::smem_desc(abase, 128, 16 * K1);
+                            const uint64_t bd0 = tc::smem_desc(b1s, 128, 16 * K1);
+                            const int nk = K1 / 16;
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) {
+                                if (j >= nk) break;
+                                tc::mma_f16(tmem, ad0 + 16ull * j, bd0 + 16ull * j, idesc1, j > 0 ? 1u : 0u);
                             }
                             tc::mma_commit(mbar1);
                         }
@@ -449,16 +455,20 @@ k_tc_rf(const TcUnit *__restrict__ units, int n_units, int64_t n_items, int *cou
                     // leading byte offset is the stride between K-adjacent core matrices
                     // (scatterer groups, 16 K1 bytes) and the stride byte offset the one
                     // between MN-adjacent core matrices (element groups, 128 bytes).
+                    // Descriptor steps in 16-byte units: k-slice j starts 2 (j mod 8) 16 K1
+                    // bytes (scatterer groups) plus (j / 8) 16 Np bytes (Im half) into the
+                    // tile, and 32 nN j bytes into B2.
                     if (tid == 0) {
+                        const uint64_t sa = (uint64_t)(2 * K1), sim = (uint64_t)Np, sb = (uint64_t)(2 * nN);
+                        const uint32_t acc0 = tile > tile0 ? 1u : 0u;
+                        const uint64_t bd0 = tc::smem_desc(b2s, 16 * nN, 128);
                         for (int h = 0; h < mh; ++h) {
                             const uint32_t d2 = tmem + (uint32_t)(nN * (1 + ((bp + bi_) * G + g) * mh + h));
-                            for (int j = 0; j < 16; ++j) {
-                                const uint32_t a0 = abase + (uint32_t)((2 * (j & 7)) * 16 * K1)
-                                                  + (uint32_t)((j >> 3) * (Np / 8) * 128) + (uint32_t)(h * 16 * 128);
-                                uint64_t ad = tc::smem_desc(a0, 16 * K1, 128);
-                                uint64_t bd = tc::smem_desc(b2s + (uint32_t)(32 * nN * j), 16 * nN, 128);
-                                tc::mma_f16(d2, ad, bd, idesc2, (j > 0 || tile > tile0) ? 1u : 0u);
-                            }
+                            const uint64_t ad0 = tc::smem_desc(abase + (uint32_t)(h * 16 * 128), 16 * K1, 128);
+#pragma unroll
+                            for (int j = 0; j < 16; ++j)
+                                tc::mma_f16(d2, ad0 + (uint64_t)(j & 7) * sa + (uint64_t)(j >> 3) * sim,
+                                            bd0 + (uint64_t)j * sb, idesc2, j > 0 ? 1u : acc0);
                         }
                         tc::mma_commit(mbar2);
                     }
