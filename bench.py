@@ -33,7 +33,10 @@ from paper_2102_02738_gb300 import phantoms as ph  # noqa: E402
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the dominant kernel, from
 # the ncu capture summarised in profiles/ (per launch; absent where the kernel changed
 # after the capture or none was taken)
-NCU_TRAFFIC = {("diverging-convex-128", "tc_f16", 100000): 53.171968e6 + 225.137408e6}
+NCU_TRAFFIC = {("diverging-convex-128", "tc_f16", 100000): 50.174720e6 + 222.333952e6,
+               ("planewave-linear-128", "plain", 20003): 1.283584e6 + 0.092160e6}
+# k_pfield on the 201 x 201 L11-5v grid (15 frequency chunks): DRAM read + write per launch
+PFIELD_TRAFFIC = 1.257114e6
 METRIC = "Green's terms/s (freq x scatterer x sub-elem x tx)"
 WORKLOADS = {
     "planewave-linear-128": ph.planewave_linear_128,
@@ -452,56 +455,137 @@ def run_batch_bench(args, rank, ws, local):
 
 
 def run_grad_bench(args, rank, ws, local):
-    """Forward RF plus the adjoint (simus_rf_grad) of the RF misfit, FP32."""
+    """Forward RF plus the adjoint (simus_rf_grad) of the RF misfit L = ||RF - RF_target||^2,
+    FP32.  The roofline is that of k_grad, which forms g, dg/dX and dg/dZ once per (bin,
+    scatterer, sub-element) for all transmits, against the forward-term ALU budget."""
     import torch
     from paper_2102_02738_gb300 import build as libbuild
     libbuild.build()
     from paper_2102_02738_gb300 import simus
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    peaks, _ = measured_peaks()
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     w = ph.planewave_linear_128_grad(**({"n_scat": args.n_scat} if args.n_scat else {}))
     path = args.path or "plain"
     plan = simus.Plan(w.cfg, path=path)
-    d = {k: torch.from_numpy(np.ascontiguousarray(getattr(w, k))).to(dev)
-         for k in ("delays", "apod", "x", "z", "rc")}
+    names = ("delays", "apod", "x", "z", "rc")
+    host = {k: np.ascontiguousarray(getattr(w, k), np.float32) for k in names}
+    d = {k: torch.from_numpy(v).to(dev) for k, v in host.items()}
     tgt = plan.rf(d["delays"], d["apod"], torch.from_numpy(w.extra["x_target"]).to(dev), None,
                   torch.from_numpy(w.extra["z_target"]).to(dev), d["rc"])
     info = plan.info
-    terms = float(info["n_bins"]) * w.n_scat * info["n_sub"] * w.cfg["n_elements"] * w.n_tx
+    M = info["n_sub"] * w.cfg["n_elements"]
+    terms = float(info["n_bins"]) * w.n_scat * M * w.n_tx
 
     def step():
         rf = plan.rf(d["delays"], d["apod"], d["x"], None, d["z"], d["rc"])
         drf = 2.0 * (rf - tgt)
-        return plan.rf_grad(d["delays"], d["apod"], d["x"], None, d["z"], d["rc"], drf)
+        return plan.rf_grad(d["delays"], d["apod"], d["x"], None, d["z"], d["rc"], drf), drf
 
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     for _ in range(max(args.warmup, 0)):
         step()
     torch.cuda.synchronize()
     simus.simus_plan_set_profiling(plan.handle, True)
+    clocks = ClockSampler(local)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
-    cur = torch.cuda.current_stream()
     fwd, bwd = [], []
+    launches0 = simus.simus_kernel_launches()
+    clocks.start()
+    time.sleep(0.5)
+    barrier(ws)
+    torch.cuda.synchronize()
     for i in range(args.steps):
-        ev[i][0].record(cur)
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
         rf = plan.rf(d["delays"], d["apod"], d["x"], None, d["z"], d["rc"])
         fwd.append(simus.simus_plan_get_timings(plan.handle))
         drf = 2.0 * (rf - tgt)
         plan.rf_grad(d["delays"], d["apod"], d["x"], None, d["z"], d["rc"], drf)
         bwd.append(simus.simus_plan_get_timings(plan.handle))
-        ev[i][1].record(cur)
+        ev[i][1].record(stream)
     torch.cuda.synchronize()
-    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    barrier(ws)
+    launches = simus.simus_kernel_launches() - launches0
+    clk = clocks.stop()
+    ms = allreduce_max(sum(a.elapsed_time(b) for a, b in ev), ws) / args.steps
     fwd_ms = statistics.mean(sum(t.values()) for t in fwd)
     bwd_ms = statistics.mean(sum(t.values()) for t in bwd)
-    line = {"metric": METRIC + ", forward + adjoint", "value": terms / (ms / 1e3), "unit": "terms/s",
-            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+    grad_ms = statistics.mean(t["gradient"] for t in bwd)
+    # k_grad's budget per (bin, scatterer): M Green's terms at the forward-term count (85
+    # FP32-pipe instructions + 12 SFU; their X/Z derivatives are not counted) and six complex
+    # contractions over (element, transmit) of 4 FMA each (P, dP/dX, dP/dZ and the three
+    # receive-side sums against the adjoint spectrum)
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    n_el = w.cfg["n_elements"]
+    cyc_pair = max((FP32_PER_TERM * M + 24.0 * n_el * w.n_tx) / 128.0, MUFU_PER_TERM * M / 16.0)
+    peak_pairs = n_sm * mhz * 1e6 / cyc_pair
+    pairs = float(info["n_bins"]) * w.n_scat
+    achieved = pairs / (grad_ms / 1e3)
+    # end to end: scatterers and transmit settings in from pinned host memory, the four
+    # gradients out to pinned host memory
+    pin = {k: torch.from_numpy(host[k]).pin_memory() for k in names}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    outs_h = None
+    e2e_ms = 0.0
+    n_e2e = max(1, min(args.steps, 5))
+    for i in range(n_e2e):
+        flush.fill_(float(i))
+        e0.record(stream)
+        for k in names:
+            d[k].copy_(pin[k], non_blocking=True)
+        g, _ = step()
+        if outs_h is None:
+            outs_h = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in g.items()}
+        for k, v in g.items():
+            outs_h[k].copy_(v, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms += e0.elapsed_time(e1)
+    e2e_ms = allreduce_max(e2e_ms, ws) / n_e2e
+    line = {"metric": METRIC + ", forward + adjoint", "value": terms * ws / (ms / 1e3), "unit": "terms/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
             "config": {"workload": "planewave-linear-128-grad", "forward_path": path,
                        "scatterers": w.n_scat, "transmits": w.n_tx, "bins": info["n_bins"],
-                       "terms_per_step": terms},
+                       "sub_elements_total": M, "terms_per_step": terms,
+                       "l2": "flushed between timed steps (256 MB write)"},
+            "roofline": {"bound": "alu", "kernel": "k_grad", "achieved": achieved / 1e9,
+                         "peak": peak_pairs / 1e9, "unit": "G(bin x scatterer)/s",
+                         "frac": achieved / peak_pairs, "traffic": None, "kernel_ms": grad_ms,
+                         "peak_source": f"SMs*clk / max((85 M + 24 N T) / 128, 12 M / 16) cycles per "
+                                        f"(bin, scatterer), M={M}, N={n_el}, T={w.n_tx}, {n_sm} SMs at {mhz} MHz"},
             "forward_ms": fwd_ms, "adjoint_ms": bwd_ms,
-            "adjoint_stages_ms": {k: statistics.mean(t[k] for t in bwd) for k in simus.STAGES}}
+            "adjoint_stages_ms": {k: statistics.mean(t[k] for t in bwd) for k in simus.STAGES},
+            "e2e": {"value": terms * ws / (e2e_ms / 1e3), "unit": "terms/s",
+                    "h2d_bytes_per_step": sum(v.numel() * 4 for v in pin.values()),
+                    "d2h_bytes_per_step": sum(v.numel() * 4 for v in outs_h.values())},
+            "gpu_launches": launches, "clocks": clk}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        # the FP64 oracle's adjoint for a sample of scatterers, from the same upstream
+        # gradient: per-scatterer gradients depend only on it and the scatterer
+        from oracle import oracle as orc
+        g, drf = step()
+        torch.cuda.synchronize()
+        sel = np.linspace(0, w.n_scat - 1, 24).astype(np.int64)
+        t0 = time.time()
+        gR, gx, gz, _ = orc.rf_grad(w.cfg, host["delays"], host["apod"], host["x"][sel], None,
+                                    host["z"][sel], host["rc"][sel], drf.double().cpu().numpy())
+        dt = time.time() - t0
+        line["cpu_baseline"] = {"value": float(info["n_bins"]) * sel.size * M * w.n_tx / dt,
+                                "unit": "terms/s", "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+                                "sample": f"adjoint only, {sel.size} of {w.n_scat} scatterers, all bins and "
+                                          f"transmits, FP64, including its DFT of the residual, {dt:.1f} s"}
+        acc = {}
+        for k, ref in (("rc", gR), ("x", gx), ("z", gz)):
+            got = g[k].double().cpu().numpy()[sel]
+            acc[k] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        line["accuracy"] = {"rel_l2_vs_fp64_oracle": acc, "tolerance": 1e-5,
+                            "compared": f"dL/dR, dL/dX, dL/dZ at {sel.size} sampled scatterers"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     plan.close()
@@ -588,7 +672,7 @@ def run_pfield_bench(args, rank, ws, local):
                        "l2": "flushed between timed steps (256 MB write)"},
             "roofline": {"bound": "alu", "kernel": "k_pfield", "achieved": achieved / 1e9,
                          "peak": peak / 1e9, "unit": "Gterm/s", "frac": achieved / peak,
-                         "traffic": None, "kernel_ms": kern_ms},
+                         "traffic": PFIELD_TRAFFIC, "kernel_ms": kern_ms},
             "e2e": {"value": terms * ws / (e2e_ms / 1e3), "unit": "terms/s",
                     "h2d_bytes_per_step": sum(v.numel() * 4 for v in pin.values()),
                     "d2h_bytes_per_step": out_h.numel() * 4},

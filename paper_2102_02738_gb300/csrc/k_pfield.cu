@@ -127,20 +127,52 @@ __global__ void k_pfield_finish(const float *__restrict__ ppart, int n_chunks, i
     }
 }
 
-// Frequency chunks (a multiple of kPQB each) until the grid fills the GPU a few times
-// over: n_fc chunks of fchunk midpoints.
-static void pfield_split(const simus_plan *p, int T, int64_t npts, int nf, int &n_fc, int &fchunk) {
-    const int64_t pblocks = ((npts + kPThreads - 1) / kPThreads) * T;
-    n_fc = 1;
-    while (n_fc < 64 && pblocks * n_fc < (int64_t)p->num_sms * 4 && (nf + 2 * n_fc - 1) / (2 * n_fc) >= 2 * kPQB)
-        n_fc *= 2;
-    fchunk = ((nf + n_fc - 1) / n_fc + kPQB - 1) / kPQB * kPQB;
-    n_fc = (nf + fchunk - 1) / fchunk;
+// Frequency chunks (a multiple of kPQB midpoints each): the count minimising the modelled
+// makespan, waves of resident blocks x (midpoints per chunk + the per-chunk geometry setup,
+// about two midpoints' work), so that the last wave is not a small remainder (with one
+// chunk per 150 midpoints the L11-5v grid ran 2.08 waves of two blocks per SM and its SMs
+// were active 79 % of the time).
+using PfieldKernel = void (*)(const GreenConst, const SubElem *, const float *, const float *,
+                              const float *, int64_t, int, int, const float2 *, const float *,
+                              float, float *, const float4 *, int, float *);
+
+static PfieldKernel pfield_kernel(const simus_plan *p, const GreenConst &gc, bool has_y) {
+    const bool narrow = gc.narrow == 1;
+    const bool tab = !has_y && p->d_dtab && gc.tab_n > 0;
+    return has_y ? (narrow ? k_pfield<true, true, false> : k_pfield<true, false, false>)
+         : tab   ? (narrow ? k_pfield<false, true, true> : k_pfield<false, false, true>)
+                 : (narrow ? k_pfield<false, true, false> : k_pfield<false, false, false>);
 }
 
-int pfield_fchunks(const simus_plan *p, int T, int64_t npts, int nf) {
+static size_t pfield_smem(const simus_plan *p) {
+    return sizeof(SubElem) * p->M + sizeof(float2) * (size_t)kPQB * p->N;
+}
+
+static void pfield_split(const simus_plan *p, PfieldKernel kern, int T, int64_t npts, int nf,
+                         int &n_fc, int &fchunk) {
+    int bps = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, kPThreads, pfield_smem(p)) != cudaSuccess)
+        bps = 1;
+    const int64_t slots = (int64_t)p->num_sms * std::max(bps, 1);
+    const int64_t pblocks = ((npts + kPThreads - 1) / kPThreads) * T;
+    n_fc = 1;
+    fchunk = (nf + kPQB - 1) / kPQB * kPQB;
+    double best = 1e300;
+    for (int n = 1; n <= 64; ++n) {
+        const int fc = ((nf + n - 1) / n + kPQB - 1) / kPQB * kPQB;
+        const int ne = (nf + fc - 1) / fc;
+        if (ne != n) continue;                     // the same split as a smaller n
+        const int64_t waves = (pblocks * ne + slots - 1) / slots;
+        const double cost = (double)waves * (fc + 2);
+        if (cost < best) { best = cost; n_fc = ne; fchunk = fc; }
+    }
+}
+
+int pfield_fchunks(const simus_plan *p, const GreenConst &gc, int T, int64_t npts, int nf, bool has_y) {
+    const PfieldKernel kern = pfield_kernel(p, gc, has_y);
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pfield_smem(p));
     int n_fc, fchunk;
-    pfield_split(p, T, npts, nf, n_fc, fchunk);
+    pfield_split(p, kern, T, npts, nf, n_fc, fchunk);
     return n_fc;
 }
 
@@ -157,16 +189,12 @@ int launch_pfield(const simus_plan *p, const GreenConst &gc, const simus_tx *tx,
         int rc = check_cuda(cudaGetLastError(), "k_pfield_weights launch");
         if (rc) return rc;
     }
-    const size_t smem = sizeof(SubElem) * p->M + sizeof(float2) * (size_t)kPQB * p->N;
-    const bool has_y = y != nullptr, narrow = gc.narrow == 1;
-    const bool tab = !has_y && p->d_dtab && gc.tab_n > 0;
-    auto kern = has_y ? (narrow ? k_pfield<true, true, false> : k_pfield<true, false, false>)
-              : tab   ? (narrow ? k_pfield<false, true, true> : k_pfield<false, false, true>)
-                      : (narrow ? k_pfield<false, true, false> : k_pfield<false, false, false>);
+    const size_t smem = pfield_smem(p);
+    const PfieldKernel kern = pfield_kernel(p, gc, y != nullptr);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return check_cuda(e, "k_pfield smem attribute");
     int n_fc, fchunk;
-    pfield_split(p, T, npts, nf, n_fc, fchunk);
+    pfield_split(p, kern, T, npts, nf, n_fc, fchunk);
     dim3 grid((unsigned)((npts + kPThreads - 1) / kPThreads), T, n_fc);
     kern<<<grid, kPThreads, smem, st>>>(gc, p->d_sub, x, y, z, npts, nf, j0, wt, ptx2, dw, prms,
                                         p->d_dtab, fchunk, n_fc > 1 ? ppart : nullptr);

@@ -190,10 +190,12 @@ PlainGeom plain_geometry(const simus_plan *p, int T, int64_t S) {
         if ((s * p->N) % kPlainThreads == 0) { SB = s; break; }
     g.SB = std::min(SB, 8);
     g.n_qtiles = (p->nq + g.QB - 1) / g.QB;
-    // enough blocks for ~8 waves of 2 blocks per SM, chunks of at least 8 groups
+    // enough blocks for ~8 waves of 2 blocks per SM, chunks of at least 4 groups (a few
+    // hundred scatterers then still fill the GPU: 0.113 -> 0.089 ms for 200 scatterers
+    // at 64 elements, against 8 groups)
     int64_t want = (int64_t)p->num_sms * 2 * 8;
     int64_t per_tx = std::max<int64_t>(1, want / std::max<int64_t>(1, (int64_t)g.n_qtiles * T));
-    int64_t min_chunk = (int64_t)g.SB * 8;
+    int64_t min_chunk = (int64_t)g.SB * 4;
     int64_t chunks = std::max<int64_t>(1, std::min<int64_t>(per_tx, (S + min_chunk - 1) / min_chunk));
     int64_t len = (S + chunks - 1) / chunks;
     len = ((len + g.SB - 1) / g.SB) * g.SB;

@@ -832,7 +832,7 @@ int simus_pfield(simus_plan *plan, const simus_tx *tx, int64_t n_pts, const floa
     const int T = tx->n_tx;
     const size_t wt_b = align256(sizeof(float2) * (size_t)T * nf * plan->N);
     const size_t p2_b = align256(sizeof(float) * nf);
-    const int n_fc = pfield_fchunks(plan, T, n_pts, nf);
+    const int n_fc = pfield_fchunks(plan, gc, T, n_pts, nf, y != nullptr);
     const size_t pp_b = n_fc > 1 ? align256(sizeof(float) * (size_t)n_fc * T * n_pts) : 0;
     void *ws;
     if ((rc = workspace(plan, wt_b + p2_b + pp_b, &ws))) return rc;

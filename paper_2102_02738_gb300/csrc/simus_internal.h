@@ -96,9 +96,10 @@ GreenConst green_const(const simus_probe &pr, const simus_medium &md, int N, int
 
 // RMS pressure field (Eq. 22, Eq. 41-42) on midpoint frequencies (j0 + jj + 1/2) gc.df,
 // jj < nf; wt: workspace [T][nf][N]; ptx2: device [nf] = |P_Tx|^2.
-// The frequencies are split into pfield_fchunks() chunks when the points alone do not fill
-// the GPU; ppart: workspace [chunks][T][npts] for their partial sums (unused for one chunk).
-int pfield_fchunks(const simus_plan *p, int T, int64_t npts, int nf);
+// The frequencies are split into pfield_fchunks() chunks (chosen with the occupancy of the
+// kernel variant that has_y and gc select); ppart: workspace [chunks][T][npts] for their
+// partial sums (unused for one chunk).
+int pfield_fchunks(const simus_plan *p, const GreenConst &gc, int T, int64_t npts, int nf, bool has_y);
 int launch_pfield(const simus_plan *p, const GreenConst &gc, const simus_tx *tx, int64_t npts,
                   const float *x, const float *y, const float *z, int nf, int j0, float2 *wt,
                   const float *ptx2, float dw, float *prms, float *ppart, cudaStream_t st);
