@@ -82,7 +82,10 @@ k_adjoint_dft(const float *__restrict__ drf, int N, int n_chan, int nq, int q_lo
 }
 
 // Shared-memory rows of N complex values are padded to Nr = N + 1 so that rows of
-// different scatterers or transmits start in different banks.
+// different scatterers or transmits start in different banks.  The sub-element records
+// are held as two float4 planes indexed [mu][e] (centroid; normal and rotated centroid),
+// so that the threads of a warp, which take consecutive elements, read consecutive
+// 16-byte words instead of 32-byte records nu apart.
 template <bool NARROW>
 __global__ void __launch_bounds__(kGThreads, 1)
 k_grad(const GreenConst gc, const SubElem *__restrict__ sub_g, const float *__restrict__ xg,
@@ -95,8 +98,9 @@ k_grad(const GreenConst gc, const SubElem *__restrict__ sub_g, const float *__re
     const int tid = threadIdx.x;
     constexpr int QB = kGQB;
     float4 *sc = reinterpret_cast<float4 *>(smem_raw);              // [SB] (x, 0, z, R)
-    SubElem *sub = reinterpret_cast<SubElem *>(sc + kGSBMax);       // [M]
-    float2 *cwt = reinterpret_cast<float2 *>(sub + M);              // [QB][T][Nr]
+    float4 *subA = sc + kGSBMax;                                     // [nu][N] xh, xl, zh, zl
+    float4 *subB = subA + M;                                        // [nu][N] cpsi, spsi, l0, z0
+    float2 *cwt = reinterpret_cast<float2 *>(subB + M);             // [QB][T][Nr]
     float2 *lat = cwt + QB * T * Nr;                                // [QB][T][Nr]
     float2 *Bt = lat + QB * T * Nr;                                 // [QB][T][N]
     float2 *Gt = Bt + QB * T * N;                                   // [3][QB][SB][Nr]
@@ -109,7 +113,12 @@ k_grad(const GreenConst gc, const SubElem *__restrict__ sub_g, const float *__re
     const int64_t s_begin = (int64_t)chunk * chunk_len;
     const int64_t s_end = min(S, s_begin + chunk_len);
 
-    for (int i = tid; i < M; i += kGThreads) sub[i] = sub_g[i];
+    for (int i = tid; i < M; i += kGThreads) {          // global [e][mu] -> shared [mu][e]
+        const float4 *r = reinterpret_cast<const float4 *>(sub_g + i);
+        const int e = i / nu, mu = i - e * nu;
+        subA[mu * N + e] = r[0];
+        subB[mu * N + e] = r[1];
+    }
     for (int i = tid; i < QB * T * N; i += kGThreads) {
         int j = i / (T * N), r = i - j * T * N, t = r / N, e = r - t * N, k = k0 + j;
         bool ok = k < nq;
@@ -144,7 +153,9 @@ k_grad(const GreenConst gc, const SubElem *__restrict__ sub_g, const float *__re
 #pragma unroll
             for (int j = 0; j < QB; ++j) G[j] = GX[j] = GZ[j] = make_float2(0.f, 0.f);
             for (int mu = 0; mu < nu; ++mu) {
-                const SubElem se = sub[e * nu + mu];
+                SubElem se;
+                reinterpret_cast<float4 *>(&se)[0] = subA[mu * N + e];
+                reinterpret_cast<float4 *>(&se)[1] = subB[mu * N + e];
                 const PairSetup P = pair_setup<false>(gc, se, ps.x, 0.f, ps.z, q0);
                 const PairGrad Q = pair_grad(gc, se, ps.x, ps.z, P);
 #pragma unroll
@@ -243,11 +254,15 @@ k_grad(const GreenConst gc, const SubElem *__restrict__ sub_g, const float *__re
         }
         __syncthreads();
 
-        // 3. B_q(t, e) += sum_s R_s A_t G_e (four elements per thread); per-scatterer
-        // gradients of this bin tile
-        const int N4 = (N + 3) >> 2;
-        for (int i = tid; i < QB * T * N4; i += kGThreads) {
-            const int j = i / (T * N4), r = i - j * T * N4, t = r / N4, e0 = (r - t * N4) * 4;
+        // 3. B_q(t, e) += sum_s R_s A_t G_e (four elements per thread, 32 apart, so that
+        // a warp reads 32 consecutive elements of a row); per-scatterer gradients of this
+        // bin tile
+        const int NC = (N + 127) >> 7;                      // chunks of 128 elements
+        for (int i = tid; i < QB * T * NC * 32; i += kGThreads) {
+            const int l = i & 31, jt = i >> 5;
+            const int jc = jt / NC, c = jt - jc * NC;
+            const int j = jc / T, t = jc - j * T;
+            const int e0 = c * 128 + l;
             float2 b[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) b[u] = make_float2(0.f, 0.f);
@@ -256,15 +271,17 @@ k_grad(const GreenConst gc, const SubElem *__restrict__ sub_g, const float *__re
                 const float2 *g = Gt + ((size_t)j * SB + s) * Nr + e0;
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    const float2 a = g[u];     // past N: the padding column or the next row, unused
-                    b[u].x = fmaf(ra.x, a.x, fmaf(-ra.y, a.y, b[u].x));
-                    b[u].y = fmaf(ra.x, a.y, fmaf(ra.y, a.x, b[u].y));
+                    if (e0 + 32 * u < N) {
+                        const float2 a = g[32 * u];
+                        b[u].x = fmaf(ra.x, a.x, fmaf(-ra.y, a.y, b[u].x));
+                        b[u].y = fmaf(ra.x, a.y, fmaf(ra.y, a.x, b[u].y));
+                    }
                 }
             }
             float2 *bt = Bt + ((size_t)j * T + t) * N + e0;
 #pragma unroll
             for (int u = 0; u < 4; ++u)
-                if (e0 + u < N) { bt[u].x += b[u].x; bt[u].y += b[u].y; }
+                if (e0 + 32 * u < N) { bt[32 * u].x += b[u].x; bt[32 * u].y += b[u].y; }
         }
         if (tid < 3 * SB) {       // fixed-order sum over (bin, transmit): reproducible
             const int which = tid / SB, s = tid - which * SB;

@@ -13,6 +13,8 @@
 //   3. accumulates RF_q(t, e) += sum_s G_e(q, s, e) R_s P_t(q, s) (Eq. 30-32) in shared
 //      memory (four elements per thread).
 // Rows of N complex values are padded to N + 1 so that rows start in different banks.
+// Sub-element records sit in shared memory as two float4 planes indexed [mu][e], so that
+// a warp, whose threads take consecutive elements, reads consecutive 16-byte words.
 // The chunk's partial spectrum goes to part[chunk][t][e][k]; chunks are summed in a fixed
 // order by the reduction kernel, so results are bitwise reproducible.
 #include <algorithm>
@@ -42,8 +44,9 @@ k_plain_mt(const GreenConst gc, const SubElem *__restrict__ sub_g, const float *
     const int N = gc.N, nu = gc.nu, M = gc.M, nq = gc.nq, Nr = N + 1;
     const int tid = threadIdx.x;
     float4 *sc = reinterpret_cast<float4 *>(smem_raw);              // [kMtSBMax] (x, y, z, R)
-    SubElem *sub = reinterpret_cast<SubElem *>(sc + kMtSBMax);      // [M]
-    float2 *cwt = reinterpret_cast<float2 *>(sub + M);              // [QB][T][Nr]
+    float4 *subA = sc + kMtSBMax;                                   // [nu][N] xh, xl, zh, zl
+    float4 *subB = subA + M;                                        // [nu][N] cpsi, spsi, l0, z0
+    float2 *cwt = reinterpret_cast<float2 *>(subB + M);             // [QB][T][Nr]
     float2 *rft = cwt + QB * T * Nr;                                // [QB][T][N]
     float2 *Gt = rft + QB * T * N;                                  // [QB][SB][Nr]
     float2 *RP = Gt + QB * SB * Nr;                                 // [QB][SB][T]
@@ -53,7 +56,12 @@ k_plain_mt(const GreenConst gc, const SubElem *__restrict__ sub_g, const float *
     const int64_t s_begin = (int64_t)chunk * chunk_len;
     const int64_t s_end = min(S, s_begin + chunk_len);
 
-    for (int i = tid; i < M; i += kMtThreads) sub[i] = sub_g[i];
+    for (int i = tid; i < M; i += kMtThreads) {         // global [e][mu] -> shared [mu][e]
+        const float4 *rec = reinterpret_cast<const float4 *>(sub_g + i);
+        const int e = i / nu, mu = i - e * nu;
+        subA[mu * N + e] = rec[0];
+        subB[mu * N + e] = rec[1];
+    }
     for (int i = tid; i < QB * T * N; i += kMtThreads) {
         const int j = i / (T * N), r = i - j * T * N, t = r / N, e = r - t * N, k = k0 + j;
         cwt[(j * T + t) * Nr + e] = k < nq ? cw[((size_t)t * nq + k) * N + e] : make_float2(0.f, 0.f);
@@ -67,7 +75,7 @@ k_plain_mt(const GreenConst gc, const SubElem *__restrict__ sub_g, const float *
     int ks = 1;
     while (ks < 8 && items * ks * 2 <= kMtThreads) ks *= 2;
     const int units = items * ks;
-    const int N4 = (N + 3) >> 2;
+    const int NC = (N + 127) >> 7;       // chunks of 128 elements
 
     for (int64_t sb = s_begin; sb < s_end; sb += SB) {
         __syncthreads();
@@ -86,7 +94,10 @@ k_plain_mt(const GreenConst gc, const SubElem *__restrict__ sub_g, const float *
 #pragma unroll
             for (int j = 0; j < QB; ++j) G[j] = make_float2(0.f, 0.f);
             for (int mu = 0; mu < nu; ++mu) {
-                const PairSetup P = pair_setup<HAS_Y>(gc, sub[e * nu + mu], ps.x, ps.y, ps.z, q0);
+                SubElem se;
+                reinterpret_cast<float4 *>(&se)[0] = subA[mu * N + e];
+                reinterpret_cast<float4 *>(&se)[1] = subB[mu * N + e];
+                const PairSetup P = pair_setup<HAS_Y>(gc, se, ps.x, ps.y, ps.z, q0);
                 float amp = P.amp0;
                 const float kt = TAB ? P.kap * gc.tab_inv_dx : 0.0f;
                 const float t0 = TAB ? gc.tab_x0 * gc.tab_inv_dx : 0.0f;
@@ -171,9 +182,13 @@ k_plain_mt(const GreenConst gc, const SubElem *__restrict__ sub_g, const float *
         }
         __syncthreads();
 
-        // 3. RF_q(t, e) += sum_s G_e R_s P_t, four elements per thread
-        for (int i = tid; i < QB * T * N4; i += kMtThreads) {
-            const int j = i / (T * N4), r = i - j * T * N4, t = r / N4, e0 = (r - t * N4) * 4;
+        // 3. RF_q(t, e) += sum_s G_e R_s P_t, four elements per thread 32 apart (a warp
+        // reads 32 consecutive elements of a row)
+        for (int i = tid; i < QB * T * NC * 32; i += kMtThreads) {
+            const int l = i & 31, jt = i >> 5;
+            const int jc = jt / NC, c = jt - jc * NC;
+            const int j = jc / T, t = jc - j * T;
+            const int e0 = c * 128 + l;
             float2 a[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) a[u] = make_float2(0.f, 0.f);
@@ -182,15 +197,17 @@ k_plain_mt(const GreenConst gc, const SubElem *__restrict__ sub_g, const float *
                 const float2 *gg = Gt + (j * SB + s) * Nr + e0;
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    const float2 v = gg[u];    // past N: padding or the next row, unused
-                    a[u].x = fmaf(v.x, rp.x, fmaf(-v.y, rp.y, a[u].x));
-                    a[u].y = fmaf(v.x, rp.y, fmaf(v.y, rp.x, a[u].y));
+                    if (e0 + 32 * u < N) {
+                        const float2 v = gg[32 * u];
+                        a[u].x = fmaf(v.x, rp.x, fmaf(-v.y, rp.y, a[u].x));
+                        a[u].y = fmaf(v.x, rp.y, fmaf(v.y, rp.x, a[u].y));
+                    }
                 }
             }
             float2 *rr = rft + (j * T + t) * N + e0;
 #pragma unroll
             for (int u = 0; u < 4; ++u)
-                if (e0 + u < N) { rr[u].x += a[u].x; rr[u].y += a[u].y; }
+                if (e0 + 32 * u < N) { rr[32 * u].x += a[u].x; rr[32 * u].y += a[u].y; }
         }
     }
     __syncthreads();
