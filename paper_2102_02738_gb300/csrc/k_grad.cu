@@ -25,6 +25,21 @@ constexpr int kGThreads = 384;  // 12 warps: the register budget of the generati
 constexpr int kGQB = 2;     // bins per tile
 constexpr int kGSBMax = 16; // scatterers per group (16, or 8 where shared memory is short)
 constexpr int kGRT = 2;     // transmits per thread in the contraction (register block)
+
+// Threads sharing one (bin, scatterer, transmit pair) item of the contraction along the
+// elements (1, 2, 4 or 8): as many as keep two items per thread or fewer.
+__host__ __device__ inline int grad_ks(int SB, int T) {
+    const int items = kGQB * SB * ((T + kGRT - 1) / kGRT);
+    int ks = 1;
+    while (ks < 8 && items * ks * 2 <= kGThreads) ks *= 2;
+    return ks;
+}
+// Row stride (complex values) of the G, dG/dX, dG/dZ tiles: N rounded up to ks mod 16, so
+// that the rows of consecutive scatterers start 2 ks words apart and the ks lanes of an item
+// (elements e, e + 1, ...) and the items of the next scatterer fall in distinct banks.
+__host__ __device__ inline int grad_row(int N, int ks) {
+    return N + (((ks - N) % 16) + 16) % 16;
+}
 }  // namespace
 
 // lam[t][k][e] = H_k sum_j drf[t][e][j] exp(-2 pi i ((q_lo + k) j mod Nt) / Nt).
@@ -81,8 +96,9 @@ k_adjoint_dft(const float *__restrict__ drf, int N, int n_chan, int nq, int q_lo
     }
 }
 
-// Shared-memory rows of N complex values are padded to Nr = N + 1 so that rows of
-// different scatterers or transmits start in different banks.  The sub-element records
+// Shared-memory rows of N complex values are padded to Nr = N + 1 (weights, adjoint
+// spectra) or NrG (Green's tiles) so that rows of different transmits or scatterers start
+// in different banks.  The sub-element records
 // are held as two float4 planes indexed [mu][e] (centroid; normal and rotated centroid),
 // so that the threads of a warp, which take consecutive elements, read consecutive
 // 16-byte words instead of 32-byte records nu apart.
@@ -97,14 +113,16 @@ k_grad(const GreenConst gc, const SubElem *__restrict__ sub_g, const float *__re
     const int N = gc.N, nu = gc.nu, M = gc.M, nq = gc.nq, Nr = N + 1;
     const int tid = threadIdx.x;
     constexpr int QB = kGQB;
+    const int ks = grad_ks(SB, T);
+    const int NrG = grad_row(N, ks);
     float4 *sc = reinterpret_cast<float4 *>(smem_raw);              // [SB] (x, 0, z, R)
     float4 *subA = sc + kGSBMax;                                     // [nu][N] xh, xl, zh, zl
     float4 *subB = subA + M;                                        // [nu][N] cpsi, spsi, l0, z0
     float2 *cwt = reinterpret_cast<float2 *>(subB + M);             // [QB][T][Nr]
     float2 *lat = cwt + QB * T * Nr;                                // [QB][T][Nr]
     float2 *Bt = lat + QB * T * Nr;                                 // [QB][T][N]
-    float2 *Gt = Bt + QB * T * N;                                   // [3][QB][SB][Nr]
-    float2 *RA = Gt + 3 * QB * SB * Nr;                             // [QB][SB][T]
+    float2 *Gt = Bt + QB * T * N;                                   // [3][QB][SB][NrG]
+    float2 *RA = Gt + 3 * QB * SB * NrG;                            // [QB][SB][T]
     float *sg = reinterpret_cast<float *>(RA + QB * SB * T);        // [3][QB*SB*T]
     const int nit = QB * SB * T;
 
@@ -128,14 +146,12 @@ k_grad(const GreenConst gc, const SubElem *__restrict__ sub_g, const float *__re
         Bt[i] = make_float2(0.f, 0.f);
     }
     const float q0 = (float)(gc.q_lo + k0);
-    const size_t plane = (size_t)QB * SB * Nr;
     // contraction work: (bin, scatterer, pair of transmits) items, each split over ks
     // threads along the elements when there are fewer items than threads
     const int TB = (T + kGRT - 1) / kGRT;
     const int items = QB * SB * TB;
-    int ks = 1;
-    while (ks < 8 && items * ks * 2 <= kGThreads) ks *= 2;
     const int units = items * ks;
+    const size_t plane = (size_t)QB * SB * NrG;
 
     for (int64_t sb = s_begin; sb < s_end; sb += SB) {
         __syncthreads();
@@ -172,7 +188,7 @@ k_grad(const GreenConst gc, const SubElem *__restrict__ sub_g, const float *__re
             }
 #pragma unroll
             for (int j = 0; j < QB; ++j) {
-                const size_t o = ((size_t)j * SB + s) * Nr + e;
+                const size_t o = ((size_t)j * SB + s) * NrG + e;
                 Gt[o] = G[j];
                 Gt[plane + o] = GX[j];
                 Gt[2 * plane + o] = GZ[j];
@@ -188,7 +204,7 @@ k_grad(const GreenConst gc, const SubElem *__restrict__ sub_g, const float *__re
             const int it = act ? w / ks : 0, part = w - (w / ks) * ks;
             const int j = it / (SB * TB), r = it - j * SB * TB, s = r / TB, tb = r - s * TB;
             const int t0 = tb * kGRT;
-            const float2 *g0 = Gt + ((size_t)j * SB + s) * Nr;
+            const float2 *g0 = Gt + ((size_t)j * SB + s) * NrG;
             const float2 *g1 = g0 + plane, *g2 = g0 + 2 * plane;
             const float2 *cr[kGRT], *lr[kGRT];
 #pragma unroll
@@ -268,7 +284,7 @@ k_grad(const GreenConst gc, const SubElem *__restrict__ sub_g, const float *__re
             for (int u = 0; u < 4; ++u) b[u] = make_float2(0.f, 0.f);
             for (int s = 0; s < SB; ++s) {
                 const float2 ra = RA[((size_t)j * SB + s) * T + t];
-                const float2 *g = Gt + ((size_t)j * SB + s) * Nr + e0;
+                const float2 *g = Gt + ((size_t)j * SB + s) * NrG + e0;
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     if (e0 + 32 * u < N) {
@@ -349,7 +365,7 @@ GradGeom grad_geometry(const simus_plan *p, int T, int64_t S) {
     auto smem_for = [&](int SB) {
         return sizeof(float4) * kGSBMax + sizeof(SubElem) * p->M
              + sizeof(float2) * (size_t)kGQB * T * Nr * 2 + sizeof(float2) * (size_t)kGQB * T * p->N
-             + sizeof(float2) * (size_t)3 * kGQB * SB * Nr
+             + sizeof(float2) * (size_t)3 * kGQB * SB * grad_row(p->N, grad_ks(SB, T))
              + sizeof(float2) * (size_t)kGQB * SB * T + sizeof(float) * 3 * kGQB * SB * T;
     };
     g.SB = smem_for(kGSBMax) <= 227 * 1024 ? kGSBMax : 8;
