@@ -65,8 +65,9 @@ k_plain_rf(const GreenConst gc, const SubElem *__restrict__ sub_g, const float *
     const int N = gc.N, nu = gc.nu, M = gc.M, nq = gc.nq;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     float4 *sc = reinterpret_cast<float4 *>(smem_raw);             // [SB] (x, y, z, R)
-    SubElem *sub = reinterpret_cast<SubElem *>(sc + SB);           // [M]
-    float2 *cwt = reinterpret_cast<float2 *>(sub + M);             // [QB][N]
+    float4 *subA = sc + SB;                                        // [nu][N] xh, xl, zh, zl
+    float4 *subB = subA + M;                                       // [nu][N] cpsi, spsi, l0, z0
+    float2 *cwt = reinterpret_cast<float2 *>(subB + M);            // [QB][N]
     float2 *acc = cwt + QB * N;                                    // [QB][N]
     float2 *RP = acc + QB * N;                                     // [QB][SB]
     float2 *Gt = RP + QB * SB;                                     // [QB][SB][N]
@@ -76,7 +77,12 @@ k_plain_rf(const GreenConst gc, const SubElem *__restrict__ sub_g, const float *
     const int64_t s_begin = (int64_t)chunk * chunk_len;
     const int64_t s_end = min(S, s_begin + chunk_len);
 
-    for (int i = tid; i < M; i += kPlainThreads) sub[i] = sub_g[i];
+    for (int i = tid; i < M; i += kPlainThreads) {      // global [e][mu] -> shared [mu][e]
+        const float4 *rec = reinterpret_cast<const float4 *>(sub_g + i);
+        const int e = i / nu, mu = i - e * nu;
+        subA[mu * N + e] = rec[0];
+        subB[mu * N + e] = rec[1];
+    }
     for (int i = tid; i < QB * N; i += kPlainThreads) {
         int j = i / N, e = i - j * N, k = k0 + j;
         cwt[i] = k < nq ? cw[((size_t)t * nq + k) * N + e] : make_float2(0.f, 0.f);
@@ -101,7 +107,10 @@ k_plain_rf(const GreenConst gc, const SubElem *__restrict__ sub_g, const float *
 #pragma unroll
             for (int j = 0; j < QB; ++j) G[j] = make_float2(0.f, 0.f);
             for (int mu = 0; mu < nu; ++mu) {
-                PairSetup P = pair_setup<HAS_Y>(gc, sub[e * nu + mu], ps.x, ps.y, ps.z, q0);
+                SubElem se;
+                reinterpret_cast<float4 *>(&se)[0] = subA[mu * N + e];
+                reinterpret_cast<float4 *>(&se)[1] = subB[mu * N + e];
+                PairSetup P = pair_setup<HAS_Y>(gc, se, ps.x, ps.y, ps.z, q0);
                 PhaseRun R = phase_run(P, q0);
                 const float kt = TAB ? P.kap * gc.tab_inv_dx : 0.0f;
                 const float t0 = TAB ? gc.tab_x0 * gc.tab_inv_dx : 0.0f;

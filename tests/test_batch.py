@@ -55,6 +55,16 @@ def test_tc_general_shapes(S, oracle, kw):
     assert rel_l2(single(S, w, "tc_f16"), oracle_rf(oracle, w)) <= TOL_TC
 
 
+@pytest.mark.parametrize("kw", [
+    dict(n_elements=150, n_sub=1, n_scat=140, n_tx=3, nt=500),     # rows of two 128-element chunks
+    dict(n_elements=192, n_sub=2, n_scat=130, n_tx=5, nt=420),
+])
+def test_plain_multi_transmit_wide_arrays(S, oracle, kw):
+    # the multi-transmit FP32 kernel accumulates RF over elements 32 apart in chunks of 128
+    w = ph.tiny(**kw)
+    assert rel_l2(single(S, w, "plain"), oracle_rf(oracle, w)) <= TOL_F32
+
+
 def ragged(n_sims=6, scale=1.0, seed=1005):
     sims = ph.ragged_batch(seed=seed, n_sims=n_sims, s_min=200, s_max=3000, scale=scale)
     for w in sims:   # keep the oracle fast: short RF records

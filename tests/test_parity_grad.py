@@ -56,6 +56,7 @@ def compare(S, oracle, w, seed=5):
     dict(convex=True, n_elements=8, n_scat=12, n_tx=2),
     dict(baffle=1, n_elements=6, n_scat=10, n_tx=2),
     dict(baffle=2, n_elements=6, n_scat=10, n_tx=2),
+    dict(n_elements=8, n_sub=2, n_scat=40, n_tx=14, nt=300),   # one lane per contraction item
 ])
 def test_grad_tiny(S, oracle, kw):
     errs = compare(S, oracle, ph.tiny(**kw))
