@@ -79,22 +79,37 @@ __device__ __forceinline__ void gen_two(const GreenConst &gc, const float4 *sub,
 #pragma unroll
             for (int c = 0; c < 2; ++c) { lo[c] = tabs[2 * ti[c]]; hi[c] = tabs[2 * ti[c] + 1]; }
         }
-        // phase, absorption and sinc directivity of every bin (common to both delta forms)
+        // phase, absorption and sinc directivity of every bin (common to both delta forms):
+        // z = amp0 exp(i 2 pi frac(qA u)) at the first bin, then z <- z w with
+        // w = mstep exp(i 2 pi frac(u)) per further bin (phase and absorption of one bin)
         float er[2][NB], ei[2][NB];
+        float zr[2], zi[2], wr[2] = {0.0f, 0.0f}, wi[2] = {0.0f, 0.0f};
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            float sn, cs;
+            sincos_a(6.283185307179586f * df_frac_mul(qA, P[c].u), sn, cs);
+            zr[c] = P[c].amp0 * cs;
+            zi[c] = P[c].amp0 * sn;
+            if (NB > 1) {
+                const float fu = (P[c].u.h - rintf(P[c].u.h)) + P[c].u.l;
+                sincos_a(6.283185307179586f * fu, sn, cs);
+                wr[c] = P[c].mstep * cs;
+                wi[c] = P[c].mstep * sn;
+            }
+        }
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
             const float q = qA + (float)b;
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
-                const float fr = df_frac_mul(q, P[c].u);
-                float sn, cs;
-                sincos_a(6.283185307179586f * fr, sn, cs);
-                float amp = P[c].amp0;
-                if (b >= 1) amp *= P[c].mstep;
-                if (b >= 2) amp *= P[c].mstep;
-                const float m = amp * sinc_f<SINC>(q * P[c].xb);
-                er[c][b] = cs * m;
-                ei[c][b] = sn * m;
+                const float m = sinc_f<SINC>(q * P[c].xb);
+                er[c][b] = zr[c] * m;
+                ei[c][b] = zi[c] * m;
+                if (b + 1 < NB) {
+                    const float nzr = fmaf(zr[c], wr[c], -zi[c] * wi[c]);
+                    zi[c] = fmaf(zr[c], wi[c], zi[c] * wr[c]);
+                    zr[c] = nzr;
+                }
             }
         }
         float2 d[2][NB];
