@@ -192,9 +192,11 @@ def run_reference(args, rank, ws):
     nu = oracle.nsub(w.cfg)
     per_bin = w.n_scat * nu * w.cfg["n_elements"] * w.n_tx
     cores = len(os.sched_getaffinity(0))
-    # each step: a fixed bin subset sized for ~3 s, so K + W steps stay within minutes
+    # each step: a fixed bin subset of at least one bin per thread (the oracle runs its
+    # bins in parallel), sized for ~3 s where a bin per thread is faster than that
     _, dt1, k1, _, _, _ = oracle_sample(w, target_s=0.0)
-    per_step_bins = max(1, min(nb, int(k1 * 3.0 / max(dt1, 1e-3))))
+    per_step_bins = max(k1, min(nb, int(k1 * 3.0 / max(dt1, 1e-3))))
+    per_step_bins = max(k1, (per_step_bins // k1) * k1)
     qs = np.linspace(lo, hi, per_step_bins).round().astype(int)
     for _ in range(args.warmup):
         oracle.rf_spectrum(w.cfg, w.delays, w.apod, w.x, w.y, w.z, w.rc, qs[:max(1, len(qs) // 4)])
