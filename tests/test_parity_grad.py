@@ -79,6 +79,22 @@ def test_grad_rejects_elevation(S):
     assert ei.value.code == -1
 
 
+def test_grad_rejects_more_than_2048_channels(S):
+    """T N > 2048 (transmit-element channels) is beyond the adjoint's shared-memory tiles:
+    SIMUS_ERR_UNSUPPORTED before any launch; the forward path still runs."""
+    w = ph.tiny(n_elements=160, n_sub=1, n_scat=10, n_tx=13, nt=300)
+    plan = S.Plan(w.cfg)
+    args = [dev(a) for a in (w.delays, w.apod, w.x, w.y, w.z, w.rc)]
+    drf = torch.zeros(w.n_tx, w.cfg["n_elements"], w.cfg["n_samples"], device="cuda")
+    with pytest.raises(S.SimusError) as ei:
+        plan.rf_grad(*args, drf)
+    assert ei.value.code == -5
+    rf = plan.rf(*args)
+    torch.cuda.synchronize()
+    assert torch.isfinite(rf).all()
+    plan.close()
+
+
 def test_autograd_misfit(S):
     """L = ||rf(x, z, R, tau) - rf_target||^2 through torch.autograd: the backward pass
     is simus_rf_grad with drf = 2 (rf - target)."""

@@ -83,6 +83,21 @@ def test_tc_bf16_error_is_reported(S, oracle):
     assert err <= 2e-2
 
 
+def test_tc_rejects_arrays_wider_than_256_elements(S):
+    """More than 256 elements do not fit one CTA's operands: the call fails before any
+    launch with SIMUS_ERR_UNSUPPORTED and the plan and the context stay usable."""
+    w = ph.tiny(n_elements=264, n_sub=1, n_scat=20, n_tx=2, nt=300)
+    plan = S.Plan(w.cfg, path="tc_f16")
+    args = [dev(a) for a in (w.delays, w.apod, w.x, w.y, w.z, w.rc)]
+    with pytest.raises(S.SimusError) as ei:
+        plan.rf(*args)
+    assert ei.value.code == -5
+    plan.close()
+    ok = ph.tiny(n_elements=8, n_scat=20, n_tx=2)
+    got, _ = run(S, ok, "tc_f16")
+    assert np.isfinite(got).all() and np.abs(got).max() > 0
+
+
 def test_tc_diverging_convex_128_sampled_bins(S, oracle):
     """Full-size 128-element convex array, 31 diverging waves, 100,000 scatterers, in the
     launch configuration the benchmark times: spectra at sampled bins vs the oracle."""
