@@ -20,7 +20,12 @@
 namespace simus {
 
 static constexpr int kPlainThreads = 256;
-static constexpr int kPlainQB = 16;
+// Bins per block tile.  With the elevation factor (3-D model) 8 bins, three blocks per SM:
+// occupancy hides the latency of the per-bin δ-table loads (planewave-linear-128 17.5 ->
+// 17.0 ms against 16 bins at two blocks); without it (2-D model) 16 bins, two blocks per
+// SM, which amortise the geometry setup over more of the cheaper bins (11.4 against 12.1 ms).
+static constexpr int kPlainQB3D = 8;
+static constexpr int kPlainQB2D = 16;
 
 // C[t][k][e] = W_te exp(i 2 pi frac(q df dtau_te)), q = q_lo + k, reduced in FP64.
 __global__ void k_tx_weights(int T, int N, int nq, int q_lo, double df,
@@ -55,7 +60,7 @@ int launch_tx_weights(const simus_plan *p, const simus_tx *tx, float2 *cw, cudaS
 // TAB: delta/h at Y = 0 from the plan's table of cubic pieces (read through the read-only
 // cache; relative error <= 2.3e-6), evaluated directly outside the table.
 template <int QB, bool HAS_Y, bool NARROW, bool TAB>
-__global__ void __launch_bounds__(kPlainThreads, 2)
+__global__ void __launch_bounds__(kPlainThreads, QB <= 8 ? 3 : 2)
 k_plain_rf(const GreenConst gc, const SubElem *__restrict__ sub_g, const float *__restrict__ xg,
            const float *__restrict__ yg, const float *__restrict__ zg,
            const float *__restrict__ rcg, int64_t S, int64_t chunk_len, int SB, int T,
@@ -191,7 +196,8 @@ static size_t plain_smem(const simus_plan *p, int QB, int SB) {
 
 PlainGeom plain_geometry(const simus_plan *p, int T, int64_t S) {
     PlainGeom g{};
-    g.QB = kPlainQB;
+    g.QB = p->gc.two_d ? kPlainQB2D : kPlainQB3D;
+    const int per_sm = g.QB <= 8 ? 3 : 2;     // resident blocks per SM (launch bounds)
     // scatterers per group: G tile within 64 KB, pairs a multiple of the block if possible
     int sb_max = std::max(1, 8192 / (g.QB * p->N));
     int SB = sb_max;
@@ -199,10 +205,10 @@ PlainGeom plain_geometry(const simus_plan *p, int T, int64_t S) {
         if ((s * p->N) % kPlainThreads == 0) { SB = s; break; }
     g.SB = std::min(SB, 8);
     g.n_qtiles = (p->nq + g.QB - 1) / g.QB;
-    // enough blocks for ~8 waves of 2 blocks per SM, chunks of at least 4 groups (a few
+    // enough blocks for ~8 waves of resident blocks, chunks of at least 4 groups (a few
     // hundred scatterers then still fill the GPU: 0.113 -> 0.089 ms for 200 scatterers
     // at 64 elements, against 8 groups)
-    int64_t want = (int64_t)p->num_sms * 2 * 8;
+    int64_t want = (int64_t)p->num_sms * per_sm * 8;
     int64_t per_tx = std::max<int64_t>(1, want / std::max<int64_t>(1, (int64_t)g.n_qtiles * T));
     int64_t min_chunk = (int64_t)g.SB * 4;
     int64_t chunks = std::max<int64_t>(1, std::min<int64_t>(per_tx, (S + min_chunk - 1) / min_chunk));
@@ -215,14 +221,25 @@ PlainGeom plain_geometry(const simus_plan *p, int T, int64_t S) {
     return g;
 }
 
+using PlainKernel = void (*)(const GreenConst, const SubElem *, const float *, const float *,
+                             const float *, const float *, int64_t, int64_t, int, int,
+                             const float2 *, float2 *, const float4 *);
+
+template <int QB>
+static PlainKernel plain_kernel(bool has_y, bool narrow, bool tab) {
+    return has_y ? (narrow ? k_plain_rf<QB, true, true, false> : k_plain_rf<QB, true, false, false>)
+         : tab   ? (narrow ? k_plain_rf<QB, false, true, true> : k_plain_rf<QB, false, false, true>)
+                 : (narrow ? k_plain_rf<QB, false, true, false> : k_plain_rf<QB, false, false, false>);
+}
+
 int launch_plain(const simus_plan *p, const PlainGeom &g, const simus_scat *sc, int T,
                  const float2 *cw, float2 *part, cudaStream_t st) {
     dim3 grid(g.n_qtiles, g.n_chunks, T);
     const bool has_y = sc->y != nullptr, narrow = p->gc.narrow == 1;
     const bool tab = !has_y && p->d_dtab && p->gc.tab_n > 0 && p->delta_table;
-    auto kern = has_y ? (narrow ? k_plain_rf<kPlainQB, true, true, false> : k_plain_rf<kPlainQB, true, false, false>)
-              : tab   ? (narrow ? k_plain_rf<kPlainQB, false, true, true> : k_plain_rf<kPlainQB, false, false, true>)
-                      : (narrow ? k_plain_rf<kPlainQB, false, true, false> : k_plain_rf<kPlainQB, false, false, false>);
+    if (g.QB != kPlainQB3D && g.QB != kPlainQB2D) return fail(SIMUS_ERR_ARG, "plain tile of %d bins", g.QB);
+    const PlainKernel kern = g.QB == kPlainQB3D ? plain_kernel<kPlainQB3D>(has_y, narrow, tab)
+                                                : plain_kernel<kPlainQB2D>(has_y, narrow, tab);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)g.smem);
     if (e != cudaSuccess) return check_cuda(e, "k_plain_rf smem attribute");
