@@ -34,7 +34,7 @@ from paper_2102_02738_gb300 import phantoms as ph  # noqa: E402
 # the ncu capture summarised in profiles/ (per launch; absent where the kernel changed
 # after the capture or none was taken)
 NCU_TRAFFIC = {("diverging-convex-128", "tc_f16", 100000): 51.287040e6 + 222.054400e6,
-               ("planewave-linear-128", "plain", 20003): 1.283584e6 + 0.092160e6}
+               ("planewave-linear-128", "plain", 20003): 1.477632e6 + 0.005120e6}
 # k_pfield on the 201 x 201 L11-5v grid (15 frequency chunks): DRAM read + write per launch
 PFIELD_TRAFFIC = 1.257114e6
 METRIC = "Green's terms/s (freq x scatterer x sub-elem x tx)"
