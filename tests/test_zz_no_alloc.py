@@ -7,7 +7,6 @@ Checks, through the C ABI: two calls in a row on different problems each match
 simus_rf on a plain FP32 plan within the FP32 tolerance (relative L2 <= 1e-5), and a
 problem whose temporaries exceed the fixed array is rejected before any device work.
 """
-import ctypes as C
 
 import numpy as np
 import pytest
