@@ -98,10 +98,10 @@ k_adjoint_dft(const float *__restrict__ drf, int N, int n_chan, int nq, int q_lo
 
 // Shared-memory rows of N complex values are padded to Nr = N + 1 (weights, adjoint
 // spectra) or NrG (Green's tiles) so that rows of different transmits or scatterers start
-// in different banks.  The sub-element records
-// are held as two float4 planes indexed [mu][e] (centroid; normal and rotated centroid),
-// so that the threads of a warp, which take consecutive elements, read consecutive
-// 16-byte words instead of 32-byte records nu apart.
+// in different banks.  The sub-element records are held as two float4 planes indexed
+// [mu][e] (centroid; normal and rotated centroid), so that the threads of a warp, which
+// take consecutive elements, read consecutive 16-byte words instead of 32-byte records
+// nu apart.
 template <bool NARROW>
 __global__ void __launch_bounds__(kGThreads, 1)
 k_grad(const GreenConst gc, const SubElem *__restrict__ sub_g, const float *__restrict__ xg,
