@@ -193,6 +193,13 @@ int simus_rf_grad(simus_plan *plan, const simus_tx *tx, const simus_scat *scat,
 int simus_batch_rf(int32_t n_sims, simus_plan *const *plans, const simus_tx *tx,
                    const simus_scat *scat, float *const *rf, void *stream);
 
+/* As simus_batch_rf, but writes each simulation's RF spectrum before the inverse DFT
+ * (Eq. 33-34), as simus_rf_spectrum does: spec[i] is device [T_i][N_i][n_bins_i][2]
+ * float32 (interleaved re, im).  The work split over the launch is the same as
+ * simus_batch_rf's for the same batch. */
+int simus_batch_rf_spectrum(int32_t n_sims, simus_plan *const *plans, const simus_tx *tx,
+                            const simus_scat *scat, float *const *spec, void *stream);
+
 /* Wait for all work queued on the plan's device, then report a failure that an earlier
  * asynchronous call on this plan met on the device: SIMUS_ERR_TIMEOUT if a bounded wait
  * inside a kernel gave up (that call's outputs are invalid; the flag is then cleared),
@@ -254,9 +261,8 @@ int64_t simus_kernel_launches(void);
 /* ---- Allocation-free RF (the paper has no counterpart; an interface for callers) -----
  * simus_rf_noalloc computes what simus_rf computes on a SIMUS_PATH_PLAIN_F32 plan built
  * from the same probe, medium and n_samples, without allocating device memory.  It is
- * for callers that cannot allocate: code running under a stream capture in global
- * capture mode (where cudaMalloc is refused), latency-critical loops that must not enter
- * an allocator (which may synchronise the device), and plug-ins whose host application
+ * for callers that cannot allocate: latency-critical loops that must not enter an
+ * allocator (which may synchronise the device), and plug-ins whose host application
  * owns the device memory.  Such callers cannot create a plan, so the probe and medium are
  * passed directly; the caller still passes the input and output arrays (device memory,
  * as for simus_rf).  Every temporary lives in one fixed device array of
@@ -265,7 +271,10 @@ int64_t simus_kernel_launches(void);
  * transmit weights T*bins*N*8 bytes, spectrum T*N*bins*8 bytes and at least one partial
  * spectrum of the same size) do not fit are rejected with SIMUS_ERR_ARG before any
  * device work.  The first call on each device resolves the array's address
- * (cudaGetSymbolAddress) with that device current: make it before any stream capture.
+ * (cudaGetSymbolAddress) with that device current.  The call uploads its two small
+ * tables from host memory with stream-ordered copies, so it cannot be recorded into a
+ * CUDA graph (a replay would read whatever a later call left in that host memory): a
+ * stream that is being captured is rejected with SIMUS_ERR_ARG before any device work.
  * All calls share the array and each keeps the previous call's contents; calls whose
  * kernels overlap on the GPU race on it (host threads are serialised, streams are not).
  * No cudaMalloc, cudaFree or allocating library routine is called. */

@@ -899,11 +899,17 @@ int simus_rf_grad(simus_plan *plan, const simus_tx *tx, const simus_scat *scat, 
     return rc;
 }
 
-int simus_batch_rf(int32_t n_sims, simus_plan *const *plans, const simus_tx *tx,
-                   const simus_scat *scat, float *const *rf, void *stream) {
-    NvtxScope nvtx_scope("simus_batch_rf");
+}  // extern "C"
+
+namespace {
+
+// Shared body of simus_batch_rf (rf != NULL) and simus_batch_rf_spectrum (spec != NULL).
+int batch_run(const char *name, int32_t n_sims, simus_plan *const *plans, const simus_tx *tx,
+              const simus_scat *scat, float *const *rf, float *const *spec, void *stream) {
+    NvtxScope nvtx_scope(name);
     CaptureScope capture_scope(stream);
-    if (n_sims < 0 || (n_sims > 0 && (!plans || !tx || !scat || !rf)))
+    float *const *out = rf ? rf : spec;
+    if (n_sims < 0 || (n_sims > 0 && (!plans || !tx || !scat || !out)))
         return fail(SIMUS_ERR_ARG, "invalid batch arguments");
     if (n_sims == 0) return SIMUS_OK;
     int rc;
@@ -916,20 +922,42 @@ int simus_batch_rf(int32_t n_sims, simus_plan *const *plans, const simus_tx *tx,
     if ((rc = use_plan_device(plans[0]))) return rc;
     for (int i = 0; i < n_sims; ++i) {
         if ((rc = validate_tx(plans[i], &tx[i])) || (rc = validate_scat(&scat[i], plans[i]->probe.two_d)) ||
-            (rc = check_device_ptr(rf[i], "rf[i]")))
+            (rc = check_device_ptr(out[i], rf ? "rf[i]" : "spec[i]")))
             return fail(rc, "simulation %d: %s", i, simus_last_error());
     }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (plans[0]->path == SIMUS_PATH_PLAIN_F32) {
         for (int i = 0; i < n_sims; ++i) {
-            const size_t bytes = sizeof(float) * (size_t)tx[i].n_tx * plans[i]->N * plans[i]->nt;
-            rc = scat[i].n == 0 ? check_cuda(cudaMemsetAsync(rf[i], 0, bytes, st), "memset rf")
-                                : plain_run(plans[i], &tx[i], &scat[i], nullptr, rf[i], st);
+            const size_t n_chan = (size_t)tx[i].n_tx * plans[i]->N;
+            float2 *sp = spec ? reinterpret_cast<float2 *>(spec[i]) : nullptr;
+            if (scat[i].n == 0)
+                rc = check_cuda(rf ? cudaMemsetAsync(rf[i], 0, sizeof(float) * n_chan * plans[i]->nt, st)
+                                   : cudaMemsetAsync(sp, 0, sizeof(float2) * n_chan * plans[i]->nq, st),
+                                "memset output");
+            else
+                rc = plain_run(plans[i], &tx[i], &scat[i], sp, rf ? rf[i] : nullptr, st);
             if (rc) return rc;
         }
         return SIMUS_OK;
     }
-    return tc_execute(plans[0], n_sims, plans, tx, scat, nullptr, rf, st);
+    if (rf) return tc_execute(plans[0], n_sims, plans, tx, scat, nullptr, rf, st);
+    std::vector<float2 *> sp(n_sims);
+    for (int i = 0; i < n_sims; ++i) sp[i] = reinterpret_cast<float2 *>(spec[i]);
+    return tc_execute(plans[0], n_sims, plans, tx, scat, sp.data(), nullptr, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+int simus_batch_rf(int32_t n_sims, simus_plan *const *plans, const simus_tx *tx,
+                   const simus_scat *scat, float *const *rf, void *stream) {
+    return batch_run("simus_batch_rf", n_sims, plans, tx, scat, rf, nullptr, stream);
+}
+
+int simus_batch_rf_spectrum(int32_t n_sims, simus_plan *const *plans, const simus_tx *tx,
+                            const simus_scat *scat, float *const *spec, void *stream) {
+    return batch_run("simus_batch_rf_spectrum", n_sims, plans, tx, scat, nullptr, spec, stream);
 }
 
 }  // extern "C"
@@ -937,22 +965,24 @@ int simus_batch_rf(int32_t n_sims, simus_plan *const *plans, const simus_tx *tx,
 // ---------------------------------------------------------------------------------
 // simus_rf_noalloc: the plain FP32 RF computation with no device allocation.
 //
-// Some callers cannot allocate device memory: code that runs while a stream is being
-// captured in global capture mode (where cudaMalloc is refused), latency-critical loops
-// that must never enter the allocator (which can synchronise the device), and plug-ins
-// hosted by an application that owns the whole device memory pool.  They cannot create
-// a plan either, so this entry point takes the probe and medium directly and keeps every
+// Some callers cannot allocate device memory: latency-critical loops that must never
+// enter the allocator (which can synchronise the device), and plug-ins hosted by an
+// application that owns the whole device memory pool.  They cannot create a plan
+// either, so this entry point takes the probe and medium directly and keeps every
 // temporary -- sub-element table, transfer values, transmit weights, per-chunk partial
 // spectra and the spectrum -- in one file-scope device array of fixed size.
 //
 // The array exists once per device that loads the library and lives until the process
 // exits.  Host code cannot use the array's name as a device address, so the first call
 // on each device (with that device current) resolves the address with
-// cudaGetSymbolAddress and caches it; make that first call before any stream capture.
-// Every call shares the array: calls that overlap on the GPU (other streams, or other
-// host threads whose kernels are still running) race on it.  Calls from several host
-// threads are serialised on the host.  Nothing in the array must start at zero: every
-// buffer is fully written before it is read.
+// cudaGetSymbolAddress and caches it.  The two small tables are uploaded from host
+// memory by stream-ordered copies; a captured copy would read that host memory when the
+// graph is replayed, after later calls have overwritten it, so a stream under capture is
+// refused before anything else is done.  Every call shares the array: calls that
+// overlap on the GPU (other streams, or other host threads whose kernels are still
+// running) race on it.  Calls from several host threads are serialised on the host.
+// Nothing in the array must start at zero: every buffer is fully written before it is
+// read.
 // ---------------------------------------------------------------------------------
 namespace {
 
@@ -974,6 +1004,15 @@ extern "C" int simus_rf_noalloc(const simus_probe *probe, const simus_medium *me
                                 float *rf, void *stream) {
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
     int dev = 0, rc;
+    {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if ((rc = check_cuda(cudaStreamIsCapturing(reinterpret_cast<cudaStream_t>(stream), &cs),
+                             "cudaStreamIsCapturing")))
+            return rc;
+        if (cs != cudaStreamCaptureStatusNone)
+            return fail(SIMUS_ERR_ARG, "simus_rf_noalloc cannot run under stream capture: its table "
+                                       "uploads read host memory that later calls overwrite");
+    }
     if ((rc = check_cuda(cudaGetDevice(&dev), "cudaGetDevice"))) return rc;
     if (dev < 0 || dev >= kNoallocMaxDevices)
         return fail(SIMUS_ERR_ARG, "device %d beyond the %d this entry point serves", dev, kNoallocMaxDevices);

@@ -89,6 +89,8 @@ def _load():
     L.simus_rf_grad.argtypes = [vp, C.POINTER(Tx), C.POINTER(Scat), vp, vp, vp, vp, vp, vp]
     L.simus_batch_rf.argtypes = [i32, C.POINTER(vp), C.POINTER(Tx), C.POINTER(Scat),
                                  C.POINTER(vp), vp]
+    L.simus_batch_rf_spectrum.argtypes = [i32, C.POINTER(vp), C.POINTER(Tx),
+                                          C.POINTER(Scat), C.POINTER(vp), vp]
     L.simus_last_error.restype = C.c_char_p
     L.simus_plan_set_profiling.argtypes = [vp, i32]
     L.simus_plan_get_timings.argtypes = [vp, C.POINTER(C.c_float)]
@@ -268,6 +270,16 @@ def simus_batch_rf(handles, txs, scats, rfs, stream=None):
     sc = (Scat * n)(*[scat_struct(*s) for s in scats])
     out = (C.c_void_p * n)(*[_dev(r, "rf") for r in rfs])
     _check(lib.simus_batch_rf(n, hs, tx, sc, out, _stream(stream)))
+
+
+def simus_batch_rf_spectrum(handles, txs, scats, specs, stream=None):
+    """specs[i]: float32 [T_i][N_i][n_bins_i][2] CUDA tensors (interleaved re, im)."""
+    n = len(handles)
+    hs = (C.c_void_p * n)(*[h.value for h in handles])
+    tx = (Tx * n)(*[tx_struct(d, a) for d, a in txs])
+    sc = (Scat * n)(*[scat_struct(*s) for s in scats])
+    out = (C.c_void_p * n)(*[_dev(r, "spec") for r in specs])
+    _check(lib.simus_batch_rf_spectrum(n, hs, tx, sc, out, _stream(stream)))
 
 
 # ------------------------------------------------------------------------- Plan
