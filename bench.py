@@ -6,6 +6,13 @@ terms + transmit and receive contractions, chunk reduction with the transfer fac
 inverse DFT to RF time signals.  Metric: Green's terms per second, one term being one
 (frequency bin x scatterer x sub-element x transmit).
 
+The default run times the 31-transmit convex workload on the FP16 tensor-core path (the
+headline), then the plain FP32 path on the same workload, and then, briefly, the other
+workloads as sub-records of the same line (``other_configs``): the 64-element focused
+and 128-element plane-wave cases on the plain path, the gradient workload (forward and
+adjoint), the ragged batch at 5 % of its scatterers under graph replay, and the convex
+workload with BF16 operands.
+
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--path P]
   python bench.py --impl reference ...     # the FP64 CPU oracle on a bounded sample
 
@@ -34,6 +41,10 @@ from paper_2102_02738_gb300 import phantoms as ph  # noqa: E402
 # after the capture or none was taken)
 NCU_TRAFFIC = {("diverging-convex-128", "tc_f16", 100000): 51.287040e6 + 222.054400e6,
                ("planewave-linear-128", "plain", 20003): 1.477632e6 + 0.005120e6}
+# thread instructions per unique Green's term of the dominant kernel, from the same
+# captures (smsp__inst_executed.sum x 32 / unique terms); used for the issue-slot fraction
+INST_PER_TERM = {("diverging-convex-128", "tc_f16", 100000): 4.527e10 * 32 / (864 * 100000 * 256),
+                 ("planewave-linear-128", "plain", 20003): 1.633e10 * 32 / (763 * 20003 * 384)}
 # k_pfield on the 201 x 201 L11-5v grid (15 frequency chunks): DRAM read + write per launch
 PFIELD_TRAFFIC = 1.257114e6
 METRIC = "Green's terms/s (freq x scatterer x sub-elem x tx)"
@@ -182,6 +193,15 @@ def oracle_sample(w, target_s=12.0, max_bins=None):
     return k * per_bin / dt, dt, k, cores, qs, X
 
 
+def workload_config(name, w, n_bins, n_sub):
+    """The workload description both arms print (the same dict for the same workload)."""
+    N = w.cfg["n_elements"]
+    return {"workload": name, "scatterers": w.n_scat, "transmits": w.n_tx, "elements": N,
+            "sub_elements": n_sub, "bins": n_bins, "rf_samples": w.cfg["n_samples"],
+            "terms_per_step": float(n_bins) * w.n_scat * n_sub * N * w.n_tx,
+            "l2": "GPU arm: flushed between timed steps (256 MB write); CPU arm: no GPU"}
+
+
 def run_reference(args, rank, ws):
     if rank != 0:
         return
@@ -211,9 +231,8 @@ def run_reference(args, rank, ws):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "path": "fp64-cpu-oracle",
-                       "scatterers": w.n_scat, "transmits": w.n_tx,
-                       "l2": "cpu"},
+            "path": "fp64-cpu-oracle",
+            "config": workload_config(args.workload, w, nb, nu),
             "cpu_baseline": {"value": value, "unit": "terms/s", "cores": cores,
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "terms/s", "h2d_bytes_per_step": 0,
@@ -223,185 +242,214 @@ def run_reference(args, rank, ws):
 
 
 # --------------------------------------------------------------------------- ours
-def run_ours(args, rank, ws, local):
-    import torch
-    from paper_2102_02738_gb300 import build as libbuild
-    libbuild.build()
-    from paper_2102_02738_gb300 import simus
+class Ctx:
+    """Device, stream, library handle and peaks shared by the measurements of one run."""
 
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    stream = torch.cuda.current_stream()
-    peaks, peak_src = measured_peaks()
-    props = torch.cuda.get_device_properties(dev)
-    n_sm = props.multi_processor_count
+    def __init__(self, local, ws):
+        import torch
+        from paper_2102_02738_gb300 import build as libbuild
+        libbuild.build()
+        from paper_2102_02738_gb300 import simus
+        torch.cuda.set_device(local)
+        self.torch, self.simus, self.local, self.ws = torch, simus, local, ws
+        self.dev = torch.device("cuda", local)
+        self.stream = torch.cuda.current_stream()
+        self.peaks, self.peak_src = measured_peaks()
+        self.n_sm = torch.cuda.get_device_properties(self.dev).multi_processor_count
+        self.mhz = float(self.peaks.get("sm_max_mhz", 2070.0))
+        self.flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=self.dev)
 
-    w = WORKLOADS[args.workload](**({"n_scat": args.n_scat} if args.n_scat else {}))
-    path = args.path or DEFAULT_PATH[args.workload]
+    def timed(self, step, steps, warmup, plans=(), flush=True):
+        """W untimed warm-up steps, then K steps each bracketed by CUDA events on the
+        launching stream (L2 flushed before each, untimed); the clocks are sampled during
+        the timed steps.  Returns per-step ms (max over ranks of the total / K for the
+        aggregate), per-step stage timings of each plan, launches and clocks."""
+        torch, simus = self.torch, self.simus
+        for _ in range(max(warmup, 0)):
+            step()
+        torch.cuda.synchronize()
+        for p in plans:
+            simus.simus_plan_set_profiling(p.handle, True)
+        clocks = ClockSampler(self.local)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        stages = [[] for _ in plans]
+        launches0 = simus.simus_kernel_launches()
+        clocks.start()
+        time.sleep(0.5)                             # let the sampler come up
+        barrier(self.ws)
+        torch.cuda.synchronize()
+        for i in range(steps):
+            if flush:
+                self.flush.fill_(float(i))        # evict L2 between timed steps (untimed)
+            ev[i][0].record(self.stream)
+            step()
+            ev[i][1].record(self.stream)
+            for j, p in enumerate(plans):
+                stages[j].append(simus.simus_plan_get_timings(p.handle))
+        torch.cuda.synchronize()
+        barrier(self.ws)
+        launches = simus.simus_kernel_launches() - launches0
+        clk = clocks.stop()
+        for p in plans:
+            simus.simus_plan_set_profiling(p.handle, False)
+        ms = [a.elapsed_time(b) for a, b in ev]
+        return ms, stages, launches, clk
+
+    def alu_peak(self):
+        return alu_peak_terms(self.n_sm, self.mhz)
+
+    def issue_frac(self, achieved, key):
+        """Fraction of the issue slots (one warp instruction per SMSP per cycle) the
+        kernel's measured instruction count per unique term takes at the achieved rate."""
+        ipt = INST_PER_TERM.get(key)
+        if ipt is None:
+            return None, None
+        return achieved * ipt / 32.0 / (self.n_sm * 4 * self.mhz * 1e6), ipt
+
+
+def dtype_of(path):
+    return "f32" if path == "plain" else ("f32+f16" if path == "tc_f16" else "f32+bf16")
+
+
+def measure_rf(ctx, name, w, path, steps, warmup, *, cpu_seconds=None, e2e=True,
+               tuning=None, oracle_ref=None):
+    """One simus_rf per step over the whole workload.  Returns the JSON line and the
+    device tensors, plan and oracle sample for follow-up measurements."""
+    torch, simus = ctx.torch, ctx.simus
     keys = ("delays", "apod", "x", "z", "rc") + (("y",) if w.y is not None else ())
     host = {k: np.ascontiguousarray(getattr(w, k)) for k in keys}
-    d = {k: torch.from_numpy(v).to(dev) for k, v in host.items()}
+    d = {k: torch.from_numpy(v).to(ctx.dev) for k, v in host.items()}
     plan = simus.Plan(w.cfg, path=path)
+    if tuning:
+        plan.set_tuning(**tuning)
     info = plan.info
     T, N, nt = w.n_tx, w.cfg["n_elements"], info["n_samples"]
-    rf = torch.empty((T, N, nt), device=dev)
+    rf = torch.empty((T, N, nt), device=ctx.dev)
     terms = metric_terms(w, info)
     # Green's terms one launch generates: once per bin for all transmits (tensor-core and
     # multi-transmit plain kernels), once per transmit only for a single transmit
     unique_per_launch = terms / T
 
     def step():
-        plan.rf(d["delays"], d["apod"], d["x"], d.get("y"), d["z"], d["rc"], out=rf, stream=stream)
+        plan.rf(d["delays"], d["apod"], d["x"], d.get("y"), d["z"], d["rc"], out=rf,
+                stream=ctx.stream)
 
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2
-    for _ in range(max(args.warmup, 0)):
-        step()
-    torch.cuda.synchronize()
-    simus.simus_plan_set_profiling(plan.handle, True)
-
-    clocks = ClockSampler(local)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    stage_ms = []
-    launches0 = simus.simus_kernel_launches()
-    clocks.start()
-    time.sleep(0.5)                             # let the sampler come up
-    barrier(ws)
-    torch.cuda.synchronize()
-    for i in range(args.steps):
-        flush.fill_(float(i))                 # evict L2 between timed steps (untimed)
-        ev[i][0].record(stream)
-        step()
-        ev[i][1].record(stream)
-        stage_ms.append(simus.simus_plan_get_timings(plan.handle))
-    torch.cuda.synchronize()
-    barrier(ws)
-    launches = simus.simus_kernel_launches() - launches0
-    clk = clocks.stop()
-    simus.simus_plan_set_profiling(plan.handle, False)
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = allreduce_max(sum(step_ms), ws)
-    ms_per_step = total_ms / args.steps
-    value = terms * ws / (ms_per_step / 1e3)
-
-    # dominant kernel: Green's terms + contraction
-    kern_ms = statistics.mean(s["green_contract"] for s in stage_ms)
+    step_ms, stages, launches, clk = ctx.timed(step, steps, warmup, plans=[plan])
+    total_ms = allreduce_max(sum(step_ms), ctx.ws)
+    ms_per_step = total_ms / steps
+    value = terms * ctx.ws / (ms_per_step / 1e3)
+    kern_ms = statistics.mean(s["green_contract"] for s in stages[0])
     achieved = unique_per_launch / (kern_ms / 1e3)
-    peak = alu_peak_terms(n_sm, float(peaks.get("sm_max_mhz", 2070.0)))
-    stage_mean = {k: statistics.mean(s[k] for s in stage_ms) for k in simus.STAGES}
-
-    # end to end through the C ABI from pinned host buffers
-    pinned = {k: torch.from_numpy(v).pin_memory() for k, v in host.items()}
-    rf_host = torch.empty((T, N, nt), dtype=torch.float32).pin_memory()
-    h2d = sum(v.numel() * 4 for v in pinned.values())
-    d2h = rf_host.numel() * 4
-    e2e_steps = max(1, min(args.steps, 5))
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e2e_ms = 0.0
-    for i in range(e2e_steps):
-        flush.fill_(float(i))
-        e0.record(stream)
-        for k in pinned:
-            d[k].copy_(pinned[k], non_blocking=True)
-        step()
-        rf_host.copy_(rf, non_blocking=True)
-        e1.record(stream)
-        e1.synchronize()
-        e2e_ms += e0.elapsed_time(e1)
-    e2e_ms = allreduce_max(e2e_ms, ws) / e2e_steps
-    e2e_value = terms * ws / (e2e_ms / 1e3)
-
-    # the plain FP32 path on the same workload (one step) for the tensor-core speed-up
-    plain = None
-    if path != "plain" and not args.no_plain_compare:
-        pplan = simus.Plan(w.cfg, path="plain")
-        simus.simus_plan_set_profiling(pplan.handle, True)
-        pplan.rf(d["delays"], d["apod"], d["x"], d.get("y"), d["z"], d["rc"], out=rf, stream=stream)
-        torch.cuda.synchronize()
-        flush.fill_(0.5)
-        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        p0.record(stream)
-        pplan.rf(d["delays"], d["apod"], d["x"], d.get("y"), d["z"], d["rc"], out=rf, stream=stream)
-        p1.record(stream)
-        p1.synchronize()
-        pms = p0.elapsed_time(p1)
-        plain = {"value": terms / (pms / 1e3), "unit": "terms/s", "ms_per_step": pms,
-                 "kernel_ms": simus.simus_plan_get_timings(pplan.handle)["green_contract"],
-                 "speedup_of_this_path": (pms / ms_per_step)}
-        pplan.close()
-
-    cpu = None
-    accuracy = None
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        v, dt, k, cores, qs, Xo = oracle_sample(w, target_s=args.cpu_seconds)
-        cpu = {"value": v, "unit": "terms/s", "cores": cores, "kind": "oracle",
-               "sample": f"RF spectrum at {k} of {info['n_bins']} kept bins, all "
-                         f"{w.n_scat} scatterers and {T} transmits, FP64, {dt:.1f} s"}
-        spec = plan.rf_spectrum(d["delays"], d["apod"], d["x"], d.get("y"), d["z"], d["rc"])
-        Xg = spec.cpu().numpy()[..., qs - info["q_lo"]]
-        accuracy = {"rel_l2_vs_fp64_oracle": float(np.linalg.norm(Xg - Xo) / np.linalg.norm(Xo)),
-                    "compared": f"RF spectra X_q(e,t) at the {k} sampled bins, every element "
-                                f"and transmit", "tolerance": 1e-5 if path == "plain" else 2e-3}
-
+    peak = ctx.alu_peak()
+    key = (name, path, w.n_scat)
+    issue, ipt = ctx.issue_frac(achieved, key)
     line = {
-        "metric": METRIC, "value": value, "unit": "terms/s", "n_gpus": ws,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "metric": METRIC, "value": value, "unit": "terms/s", "n_gpus": ctx.ws,
+        "steps": steps, "warmup": warmup, "ms_per_step": ms_per_step,
+        "ms_per_step_median": statistics.median(step_ms),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32" if path == "plain" else ("f32+f16" if path == "tc_f16" else "f32+bf16"),
-        "data": "synthetic",
-        "config": {"workload": args.workload, "path": path, "scatterers": w.n_scat,
-                   "transmits": T, "elements": N, "sub_elements": info["n_sub"],
-                   "bins": info["n_bins"], "rf_samples": nt,
-                   "terms_per_step": terms, "l2": "flushed between timed steps (256 MB write)",
-                   "parallelism": "replicas" if ws > 1 else "single-gpu"},
+        "dtype": dtype_of(path), "data": "synthetic", "path": path,
+        "config": workload_config(name, w, info["n_bins"], info["n_sub"]),
         "roofline": {"bound": "alu", "kernel": "green+contraction",
                      "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gterm/s",
                      "frac": achieved / peak,
-                     "traffic": NCU_TRAFFIC.get((args.workload, path, w.n_scat)),
-                     "peak_source": f"{peak_src}: min(SMs*128*clk/{FP32_PER_TERM}, "
-                                    f"SMs*16*clk/{MUFU_PER_TERM}), {n_sm} SMs at "
-                                    f"{peaks.get('sm_max_mhz', 2070.0)} MHz",
+                     "traffic": NCU_TRAFFIC.get(key),
+                     "peak_source": f"{ctx.peak_src}: min(SMs*128*clk/{FP32_PER_TERM}, "
+                                    f"SMs*16*clk/{MUFU_PER_TERM}), {ctx.n_sm} SMs at "
+                                    f"{ctx.mhz} MHz",
+                     "issue_frac": issue,
+                     "inst_per_term": ipt,
+                     "issue_source": ("thread instructions per unique term from the ncu "
+                                      "capture of this kernel (smsp__inst_executed.sum x 32 / "
+                                      "terms); issue slots = SMs x 4 SMSPs x clk"
+                                      if ipt else "no capture of the current kernel"),
                      "kernel_ms": kern_ms},
-        "stages_ms": stage_mean,
-        "e2e": {"value": e2e_value, "unit": "terms/s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
+        "stages_ms": {k: statistics.mean(s[k] for s in stages[0]) for k in simus.STAGES},
         "gpu_launches": launches,
         "clocks": clk,
     }
-    if cpu is not None:
-        line["cpu_baseline"] = cpu
-    if accuracy is not None:
-        line["accuracy"] = accuracy
-    if plain is not None:
-        line["plain_f32_same_workload"] = plain
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    plan.close()
+    if tuning:
+        line["tuning"] = dict(tuning)
+    if e2e:
+        # end to end through the C ABI from pinned host buffers
+        pinned = {k: torch.from_numpy(v).pin_memory() for k, v in host.items()}
+        rf_host = torch.empty((T, N, nt), dtype=torch.float32).pin_memory()
+        h2d = sum(v.numel() * 4 for v in pinned.values())
+        d2h = rf_host.numel() * 4
+        e2e_steps = max(1, min(steps, 5))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e2e_ms = 0.0
+        for i in range(e2e_steps):
+            ctx.flush.fill_(float(i))
+            e0.record(ctx.stream)
+            for k in pinned:
+                d[k].copy_(pinned[k], non_blocking=True)
+            step()
+            rf_host.copy_(rf, non_blocking=True)
+            e1.record(ctx.stream)
+            e1.synchronize()
+            e2e_ms += e0.elapsed_time(e1)
+        e2e_ms = allreduce_max(e2e_ms, ctx.ws) / e2e_steps
+        line["e2e"] = {"value": terms * ctx.ws / (e2e_ms / 1e3), "unit": "terms/s",
+                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+    ref = oracle_ref
+    if ref is None and cpu_seconds is not None and ctx.ws == 1:
+        v, dt, k, cores, qs, Xo = oracle_sample(w, target_s=cpu_seconds)
+        ref = (qs, Xo)
+        line["cpu_baseline"] = {
+            "value": v, "unit": "terms/s", "cores": cores, "kind": "oracle",
+            "sample": f"RF spectrum at {k} of {info['n_bins']} kept bins, all "
+                      f"{w.n_scat} scatterers and {T} transmits, FP64, {dt:.1f} s"}
+    if ref is not None:
+        qs, Xo = ref
+        spec = plan.rf_spectrum(d["delays"], d["apod"], d["x"], d.get("y"), d["z"], d["rc"])
+        Xg = spec.cpu().numpy()[..., qs - info["q_lo"]]
+        line["accuracy"] = {
+            "rel_l2_vs_fp64_oracle": float(np.linalg.norm(Xg - Xo) / np.linalg.norm(Xo)),
+            "compared": f"RF spectra X_q(e,t) at {len(qs)} sampled bins, every element and "
+                        f"transmit", "tolerance": 1e-5 if path == "plain" else 2e-3}
+    return line, {"plan": plan, "d": d, "rf": rf, "terms": terms, "ref": ref}
 
 
-def run_batch_bench(args, rank, ws, local):
+def measure_plain_compare(ctx, w, st, steps):
+    """The plain FP32 path on the same workload and device tensors, timed like the
+    headline (warm-up, L2 flush, CUDA events per step); median and spread."""
+    simus = ctx.simus
+    d, rf = st["d"], st["rf"]
+    pplan = simus.Plan(w.cfg, path="plain")
+
+    def step():
+        pplan.rf(d["delays"], d["apod"], d["x"], d.get("y"), d["z"], d["rc"], out=rf,
+                 stream=ctx.stream)
+
+    ms, stages, _, clk = ctx.timed(step, steps, 1, plans=[pplan])
+    med = statistics.median(ms)
+    pplan.close()
+    return {"value": st["terms"] / (med / 1e3), "unit": "terms/s", "steps": steps,
+            "ms_per_step_median": med, "ms_per_step_min": min(ms), "ms_per_step_max": max(ms),
+            "kernel_ms_median": statistics.median(s["green_contract"] for s in stages[0]),
+            "clocks": clk}
+
+
+def measure_batch(ctx, n_sims, scale, path, steps, warmup):
     """Ragged batch: every simulation in one persistent tensor-core launch per step; the
     whole simus_batch_rf call is captured once in a CUDA graph and replayed."""
-    import torch
-    from paper_2102_02738_gb300 import build as libbuild
-    libbuild.build()
-    from paper_2102_02738_gb300 import simus
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    sims = ph.ragged_batch(n_sims=args.n_sims, scale=args.scale)
-    path = args.path or "tc_f16"
+    torch, simus = ctx.torch, ctx.simus
+    sims = ph.ragged_batch(n_sims=n_sims, scale=scale)
     plans = [simus.Plan(w.cfg, path=path) for w in sims]
-    txs = [(torch.from_numpy(w.delays).to(dev), torch.from_numpy(w.apod).to(dev)) for w in sims]
-    scs = [(torch.from_numpy(w.x).to(dev), None, torch.from_numpy(w.z).to(dev),
-            torch.from_numpy(w.rc).to(dev)) for w in sims]
-    rfs = [torch.empty((w.n_tx, w.cfg["n_elements"], p.info["n_samples"]), device=dev)
+    txs = [(torch.from_numpy(w.delays).to(ctx.dev), torch.from_numpy(w.apod).to(ctx.dev))
+           for w in sims]
+    scs = [(torch.from_numpy(w.x).to(ctx.dev), None, torch.from_numpy(w.z).to(ctx.dev),
+            torch.from_numpy(w.rc).to(ctx.dev)) for w in sims]
+    rfs = [torch.empty((w.n_tx, w.cfg["n_elements"], p.info["n_samples"]), device=ctx.dev)
            for w, p in zip(sims, plans)]
     terms = sum(float(p.info["n_bins"]) * w.n_scat * p.info["n_sub"] * w.cfg["n_elements"] * w.n_tx
                 for w, p in zip(sims, plans))
     unique = sum(float(p.info["n_bins"]) * w.n_scat * p.info["n_sub"] * w.cfg["n_elements"]
                  for w, p in zip(sims, plans))
-    st = torch.cuda.Stream(device=dev)
+    st = torch.cuda.Stream(device=ctx.dev)
     handles = [p.handle for p in plans]
     with torch.cuda.stream(st):
         simus.simus_batch_rf(handles, txs, scs, rfs, st)            # sizes workspaces
@@ -411,108 +459,62 @@ def run_batch_bench(args, rank, ws, local):
     with torch.cuda.graph(g, stream=st):
         simus.simus_batch_rf(handles, txs, scs, rfs, st)
     per_replay = simus.simus_kernel_launches() - l0
-    for _ in range(max(args.warmup, 0)):
-        g.replay()
-    torch.cuda.synchronize()
-    clocks = ClockSampler(local)
-    clocks.start()
-    time.sleep(0.5)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    barrier(ws)
-    torch.cuda.synchronize()
-    cur = torch.cuda.current_stream()
-    for i in range(args.steps):
-        ev[i][0].record(cur)
-        g.replay()
-        ev[i][1].record(cur)
-    torch.cuda.synchronize()
-    barrier(ws)
-    clk = clocks.stop()
-    ms = allreduce_max(sum(a.elapsed_time(b) for a, b in ev), ws) / args.steps
-    peaks, peak_src = measured_peaks()
-    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak = alu_peak_terms(n_sm, float(peaks.get("sm_max_mhz", 2070.0)))
-    line = {"metric": METRIC, "value": terms * ws / (ms / 1e3), "unit": "terms/s", "n_gpus": ws,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+    # inputs and outputs of the batch exceed L2 at full scale; the replay is timed as is
+    ms, _, _, clk = ctx.timed(g.replay, steps, warmup, flush=scale < 0.5)
+    ms_step = allreduce_max(sum(ms), ctx.ws) / steps
+    peak = ctx.alu_peak()
+    line = {"metric": METRIC, "value": terms * ctx.ws / (ms_step / 1e3), "unit": "terms/s",
+            "n_gpus": ctx.ws, "steps": steps, "warmup": warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32+f16" if path == "tc_f16" else path, "data": "synthetic",
-            "config": {"workload": "ragged-batch", "sims": len(sims), "scale": args.scale,
+            "dtype": dtype_of(path), "data": "synthetic", "path": path,
+            "config": {"workload": "ragged-batch", "sims": len(sims), "scale": scale,
                        "scatterers_total": int(sum(w.n_scat for w in sims)),
                        "elements": [min(w.cfg["n_elements"] for w in sims), max(w.cfg["n_elements"] for w in sims)],
                        "transmits": [min(w.n_tx for w in sims), max(w.n_tx for w in sims)],
                        "terms_per_step": terms, "unique_terms_per_step": unique,
                        "execution": "one persistent launch per step, captured CUDA graph",
-                       "l2": "inputs and outputs exceed L2"},
-            "roofline": {"bound": "alu", "achieved": unique / (ms / 1e3) / 1e9, "peak": peak / 1e9,
-                         "unit": "Gterm/s", "frac": unique / (ms / 1e3) / peak,
+                       "l2": ("inputs and outputs exceed L2" if scale >= 0.5 else
+                              "flushed between timed steps (256 MB write)")},
+            "roofline": {"bound": "alu", "achieved": unique / (ms_step / 1e3) / 1e9, "peak": peak / 1e9,
+                         "unit": "Gterm/s", "frac": unique / (ms_step / 1e3) / peak,
                          "note": "whole step (weights + persistent kernel + reductions + iDFTs)",
-                         "peak_source": peak_src},
-            "gpu_launches": per_replay * args.steps, "clocks": clk}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+                         "peak_source": ctx.peak_src},
+            "gpu_launches": per_replay * steps, "clocks": clk}
     for p in plans:
         p.close()
+    return line
 
 
-def run_grad_bench(args, rank, ws, local):
+def measure_grad(ctx, steps, warmup, path="plain", n_scat=0, accuracy=True):
     """Forward RF plus the adjoint (simus_rf_grad) of the RF misfit L = ||RF - RF_target||^2,
     FP32.  The roofline is that of k_grad, which forms g, dg/dX and dg/dZ once per (bin,
     scatterer, sub-element) for all transmits, against the forward-term ALU budget."""
-    import torch
-    from paper_2102_02738_gb300 import build as libbuild
-    libbuild.build()
-    from paper_2102_02738_gb300 import simus
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    stream = torch.cuda.current_stream()
-    peaks, _ = measured_peaks()
-    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-    w = ph.planewave_linear_128_grad(**({"n_scat": args.n_scat} if args.n_scat else {}))
-    path = args.path or "plain"
+    torch, simus = ctx.torch, ctx.simus
+    w = ph.planewave_linear_128_grad(**({"n_scat": n_scat} if n_scat else {}))
     plan = simus.Plan(w.cfg, path=path)
     names = ("delays", "apod", "x", "z", "rc")
     host = {k: np.ascontiguousarray(getattr(w, k), np.float32) for k in names}
-    d = {k: torch.from_numpy(v).to(dev) for k, v in host.items()}
-    tgt = plan.rf(d["delays"], d["apod"], torch.from_numpy(w.extra["x_target"]).to(dev), None,
-                  torch.from_numpy(w.extra["z_target"]).to(dev), d["rc"])
+    d = {k: torch.from_numpy(v).to(ctx.dev) for k, v in host.items()}
+    tgt = plan.rf(d["delays"], d["apod"], torch.from_numpy(w.extra["x_target"]).to(ctx.dev), None,
+                  torch.from_numpy(w.extra["z_target"]).to(ctx.dev), d["rc"])
     info = plan.info
     M = info["n_sub"] * w.cfg["n_elements"]
     terms = float(info["n_bins"]) * w.n_scat * M * w.n_tx
-
-    def step():
-        rf = plan.rf(d["delays"], d["apod"], d["x"], None, d["z"], d["rc"])
-        drf = 2.0 * (rf - tgt)
-        return plan.rf_grad(d["delays"], d["apod"], d["x"], None, d["z"], d["rc"], drf), drf
-
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    for _ in range(max(args.warmup, 0)):
-        step()
-    torch.cuda.synchronize()
-    simus.simus_plan_set_profiling(plan.handle, True)
-    clocks = ClockSampler(local)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
     fwd, bwd = [], []
-    launches0 = simus.simus_kernel_launches()
-    clocks.start()
-    time.sleep(0.5)
-    barrier(ws)
-    torch.cuda.synchronize()
-    for i in range(args.steps):
-        flush.fill_(float(i))
-        ev[i][0].record(stream)
+
+    def step(record=False):
         rf = plan.rf(d["delays"], d["apod"], d["x"], None, d["z"], d["rc"])
-        fwd.append(simus.simus_plan_get_timings(plan.handle))
+        if record:
+            fwd.append(simus.simus_plan_get_timings(plan.handle))
         drf = 2.0 * (rf - tgt)
-        plan.rf_grad(d["delays"], d["apod"], d["x"], None, d["z"], d["rc"], drf)
-        bwd.append(simus.simus_plan_get_timings(plan.handle))
-        ev[i][1].record(stream)
-    torch.cuda.synchronize()
-    barrier(ws)
-    launches = simus.simus_kernel_launches() - launches0
-    clk = clocks.stop()
-    ms = allreduce_max(sum(a.elapsed_time(b) for a, b in ev), ws) / args.steps
+        g = plan.rf_grad(d["delays"], d["apod"], d["x"], None, d["z"], d["rc"], drf)
+        if record:
+            bwd.append(simus.simus_plan_get_timings(plan.handle))
+        return g
+
+    ms, _, launches, clk = ctx.timed(lambda: step(True), steps, warmup, plans=[plan])
+    fwd, bwd = fwd[-steps:], bwd[-steps:]
+    ms_step = allreduce_max(sum(ms), ctx.ws) / steps
     fwd_ms = statistics.mean(sum(t.values()) for t in fwd)
     bwd_ms = statistics.mean(sum(t.values()) for t in bwd)
     grad_ms = statistics.mean(t["gradient"] for t in bwd)
@@ -520,10 +522,9 @@ def run_grad_bench(args, rank, ws, local):
     # FP32-pipe instructions + 12 SFU; their X/Z derivatives are not counted) and six complex
     # contractions over (element, transmit) of 4 FMA each (P, dP/dX, dP/dZ and the three
     # receive-side sums against the adjoint spectrum)
-    mhz = float(peaks.get("sm_max_mhz", 2070.0))
     n_el = w.cfg["n_elements"]
     cyc_pair = max((FP32_PER_TERM * M + 24.0 * n_el * w.n_tx) / 128.0, MUFU_PER_TERM * M / 16.0)
-    peak_pairs = n_sm * mhz * 1e6 / cyc_pair
+    peak_pairs = ctx.n_sm * ctx.mhz * 1e6 / cyc_pair
     pairs = float(info["n_bins"]) * w.n_scat
     achieved = pairs / (grad_ms / 1e3)
     # end to end: scatterers and transmit settings in from pinned host memory, the four
@@ -532,25 +533,25 @@ def run_grad_bench(args, rank, ws, local):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     outs_h = None
     e2e_ms = 0.0
-    n_e2e = max(1, min(args.steps, 5))
+    n_e2e = max(1, min(steps, 5))
     for i in range(n_e2e):
-        flush.fill_(float(i))
-        e0.record(stream)
+        ctx.flush.fill_(float(i))
+        e0.record(ctx.stream)
         for k in names:
             d[k].copy_(pin[k], non_blocking=True)
-        g, _ = step()
+        g = step()
         if outs_h is None:
             outs_h = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in g.items()}
         for k, v in g.items():
             outs_h[k].copy_(v, non_blocking=True)
-        e1.record(stream)
+        e1.record(ctx.stream)
         e1.synchronize()
         e2e_ms += e0.elapsed_time(e1)
-    e2e_ms = allreduce_max(e2e_ms, ws) / n_e2e
-    line = {"metric": METRIC + ", forward + adjoint", "value": terms * ws / (ms / 1e3), "unit": "terms/s",
-            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32", "data": "synthetic",
+    e2e_ms = allreduce_max(e2e_ms, ctx.ws) / n_e2e
+    line = {"metric": METRIC + ", forward + adjoint", "value": terms * ctx.ws / (ms_step / 1e3),
+            "unit": "terms/s", "n_gpus": ctx.ws, "steps": steps, "warmup": warmup,
+            "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "path": path,
             "config": {"workload": "planewave-linear-128-grad", "forward_path": path,
                        "scatterers": w.n_scat, "transmits": w.n_tx, "bins": info["n_bins"],
                        "sub_elements_total": M, "terms_per_step": terms,
@@ -559,50 +560,47 @@ def run_grad_bench(args, rank, ws, local):
                          "peak": peak_pairs / 1e9, "unit": "G(bin x scatterer)/s",
                          "frac": achieved / peak_pairs, "traffic": None, "kernel_ms": grad_ms,
                          "peak_source": f"SMs*clk / max((85 M + 24 N T) / 128, 12 M / 16) cycles per "
-                                        f"(bin, scatterer), M={M}, N={n_el}, T={w.n_tx}, {n_sm} SMs at {mhz} MHz"},
+                                        f"(bin, scatterer), M={M}, N={n_el}, T={w.n_tx}, "
+                                        f"{ctx.n_sm} SMs at {ctx.mhz} MHz"},
             "forward_ms": fwd_ms, "adjoint_ms": bwd_ms,
             "adjoint_stages_ms": {k: statistics.mean(t[k] for t in bwd) for k in simus.STAGES},
-            "e2e": {"value": terms * ws / (e2e_ms / 1e3), "unit": "terms/s",
+            "e2e": {"value": terms * ctx.ws / (e2e_ms / 1e3), "unit": "terms/s",
                     "h2d_bytes_per_step": sum(v.numel() * 4 for v in pin.values()),
                     "d2h_bytes_per_step": sum(v.numel() * 4 for v in outs_h.values())},
             "gpu_launches": launches, "clocks": clk}
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        # the FP64 oracle's adjoint for a sample of scatterers, from the same upstream
+    if accuracy and ctx.ws == 1:
+        # the FP64 oracle's adjoint for a sample of scatterers from a seeded upstream
         # gradient: per-scatterer gradients depend only on it and the scatterer
         from oracle import oracle as orc
-        g, drf = step()
+        T, nt = w.n_tx, info["n_samples"]
+        drf = ph.normal(1004, 31, T * n_el * nt).reshape(T, n_el, nt).astype(np.float32)
+        g = plan.rf_grad(d["delays"], d["apod"], d["x"], None, d["z"], d["rc"],
+                         torch.from_numpy(drf).to(ctx.dev))
         torch.cuda.synchronize()
         sel = np.linspace(0, w.n_scat - 1, 24).astype(np.int64)
         t0 = time.time()
         gR, gx, gz, _ = orc.rf_grad(w.cfg, host["delays"], host["apod"], host["x"][sel], None,
-                                    host["z"][sel], host["rc"][sel], drf.double().cpu().numpy())
+                                    host["z"][sel], host["rc"][sel], drf)
         dt = time.time() - t0
         line["cpu_baseline"] = {"value": float(info["n_bins"]) * sel.size * M * w.n_tx / dt,
                                 "unit": "terms/s", "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
                                 "sample": f"adjoint only, {sel.size} of {w.n_scat} scatterers, all bins and "
-                                          f"transmits, FP64, including its DFT of the residual, {dt:.1f} s"}
+                                          f"transmits, FP64, including its DFT of the upstream gradient, "
+                                          f"{dt:.1f} s"}
         acc = {}
         for k, ref in (("rc", gR), ("x", gx), ("z", gz)):
             got = g[k].double().cpu().numpy()[sel]
             acc[k] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
         line["accuracy"] = {"rel_l2_vs_fp64_oracle": acc, "tolerance": 1e-5,
-                            "compared": f"dL/dR, dL/dX, dL/dZ at {sel.size} sampled scatterers"}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+                            "compared": f"dL/dR, dL/dX, dL/dZ at {sel.size} sampled scatterers of "
+                                        f"the full workload, seeded upstream gradient"}
     plan.close()
+    return line
 
 
-def run_pfield_bench(args, rank, ws, local):
+def measure_pfield(ctx, steps, warmup, accuracy=True):
     """RMS field (Eq. 41-42) of the Fig. 10 L11-5v setup on a 201 x 201 x-z grid, FP32."""
-    import torch
-    from paper_2102_02738_gb300 import build as libbuild
-    libbuild.build()
-    from paper_2102_02738_gb300 import simus
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    stream = torch.cuda.current_stream()
-    peaks, _ = measured_peaks()
-    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    torch, simus = ctx.torch, ctx.simus
     w = ph.pfield_l11_5v()
     cfg = w.cfg
     plan = simus.Plan(cfg, path="plain")
@@ -610,75 +608,52 @@ def run_pfield_bench(args, rank, ws, local):
     r_max = float(np.max(np.hypot(w.x[:, None] - xe[None, :], w.z[:, None] - ze[None, :]))) + cfg["width"]
     nf = simus.simus_pfield_nfreq(cfg, r_max, float(w.delays.max()))
     host = {k: np.ascontiguousarray(getattr(w, k)) for k in ("delays", "apod", "x", "z")}
-    d = {k: torch.from_numpy(v).to(dev) for k, v in host.items()}
+    d = {k: torch.from_numpy(v).to(ctx.dev) for k, v in host.items()}
     npts = w.x.size
-    out = torch.empty((w.n_tx, npts), device=dev)
+    out = torch.empty((w.n_tx, npts), device=ctx.dev)
     M = plan.info["n_sub"] * cfg["n_elements"]
     terms = float(npts) * nf * M * w.n_tx
 
     def step():
-        plan.pfield(d["delays"], d["apod"], d["x"], None, d["z"], nf, out=out, stream=stream)
+        plan.pfield(d["delays"], d["apod"], d["x"], None, d["z"], nf, out=out, stream=ctx.stream)
 
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    for _ in range(max(args.warmup, 0)):
-        step()
-    torch.cuda.synchronize()
-    simus.simus_plan_set_profiling(plan.handle, True)
-    clocks = ClockSampler(local)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    stage_ms = []
-    launches0 = simus.simus_kernel_launches()
-    clocks.start()
-    time.sleep(0.5)
-    barrier(ws)
-    torch.cuda.synchronize()
-    for i in range(args.steps):
-        flush.fill_(float(i))
-        ev[i][0].record(stream)
-        step()
-        ev[i][1].record(stream)
-        stage_ms.append(simus.simus_plan_get_timings(plan.handle))
-    torch.cuda.synchronize()
-    barrier(ws)
-    launches = simus.simus_kernel_launches() - launches0
-    clk = clocks.stop()
-    ms_per_step = allreduce_max(sum(a.elapsed_time(b) for a, b in ev), ws) / args.steps
-    kern_ms = statistics.mean(s["pfield"] for s in stage_ms)
-    peak = alu_peak_terms(n_sm, float(peaks.get("sm_max_mhz", 2070.0)))
+    ms, stages, launches, clk = ctx.timed(step, steps, warmup, plans=[plan])
+    ms_per_step = allreduce_max(sum(ms), ctx.ws) / steps
+    kern_ms = statistics.mean(s["pfield"] for s in stages[0])
+    peak = ctx.alu_peak()
     achieved = terms / (kern_ms / 1e3)
     # end to end: grid coordinates in, field out, through pinned host buffers
     pin = {k: torch.from_numpy(host[k]).pin_memory() for k in ("x", "z")}
     out_h = torch.empty((w.n_tx, npts), dtype=torch.float32).pin_memory()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e2e_ms = 0.0
-    n_e2e = max(1, min(args.steps, 5))
+    n_e2e = max(1, min(steps, 5))
     for i in range(n_e2e):
-        flush.fill_(float(i))
-        e0.record(stream)
+        ctx.flush.fill_(float(i))
+        e0.record(ctx.stream)
         for k in pin:
             d[k].copy_(pin[k], non_blocking=True)
         step()
         out_h.copy_(out, non_blocking=True)
-        e1.record(stream)
+        e1.record(ctx.stream)
         e1.synchronize()
         e2e_ms += e0.elapsed_time(e1)
-    e2e_ms = allreduce_max(e2e_ms, ws) / n_e2e
-    line = {"metric": METRIC.replace("scatterer", "field point"), "value": terms * ws / (ms_per_step / 1e3),
-            "unit": "terms/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+    e2e_ms = allreduce_max(e2e_ms, ctx.ws) / n_e2e
+    line = {"metric": METRIC.replace("scatterer", "field point"), "value": terms * ctx.ws / (ms_per_step / 1e3),
+            "unit": "terms/s", "n_gpus": ctx.ws, "steps": steps, "warmup": warmup,
             "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "path": "plain",
             "config": {"workload": "pfield-l11-5v", "points": npts, "frequencies": nf,
                        "sub_elements_total": M, "transmits": w.n_tx, "terms_per_step": terms,
                        "l2": "flushed between timed steps (256 MB write)"},
             "roofline": {"bound": "alu", "kernel": "k_pfield", "achieved": achieved / 1e9,
                          "peak": peak / 1e9, "unit": "Gterm/s", "frac": achieved / peak,
                          "traffic": PFIELD_TRAFFIC, "kernel_ms": kern_ms},
-            "e2e": {"value": terms * ws / (e2e_ms / 1e3), "unit": "terms/s",
+            "e2e": {"value": terms * ctx.ws / (e2e_ms / 1e3), "unit": "terms/s",
                     "h2d_bytes_per_step": sum(v.numel() * 4 for v in pin.values()),
                     "d2h_bytes_per_step": out_h.numel() * 4},
             "gpu_launches": launches, "clocks": clk}
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+    if accuracy and ctx.ws == 1:
         from oracle import oracle as orc
         sel = np.linspace(0, npts - 1, 60).astype(np.int64)
         t0 = time.time()
@@ -690,9 +665,76 @@ def run_pfield_bench(args, rank, ws, local):
                                 "sample": f"{sel.size} of {npts} grid points, all {nf} frequencies, FP64, {dt:.1f} s"}
         line["accuracy"] = {"rel_l2_vs_fp64_oracle": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
                             "compared": f"RMS pressure at the {sel.size} sampled points", "tolerance": 1e-5}
+    plan.close()
+    return line
+
+
+SUB_KEYS = ("ms_per_step", "ms_per_step_median", "value", "unit", "steps", "path", "dtype",
+            "forward_ms", "adjoint_ms", "accuracy", "tuning")
+
+
+def compact(line):
+    """The sub-record of another workload inside the headline line."""
+    out = {k: line[k] for k in SUB_KEYS if k in line}
+    out["config"] = {k: v for k, v in line["config"].items() if k != "l2"}
+    r = line["roofline"]
+    out["roofline"] = {k: r[k] for k in ("kernel", "achieved", "peak", "unit", "frac", "kernel_ms",
+                                         "issue_frac") if k in r}
+    out["clocks"] = {k: line["clocks"].get(k) for k in ("sm_mhz", "reasons")}
+    return out
+
+
+def other_configs(ctx, headline_ref):
+    """The other workloads, measured briefly after the headline (single GPU only)."""
+    out = {}
+    t0 = time.time()
+    w = ph.focused_linear_64()
+    line, st = measure_rf(ctx, "focused-linear-64", w, "plain", 10, 3, cpu_seconds=1.0, e2e=False)
+    st["plan"].close()
+    out["focused-linear-64"] = compact(line)
+    w = ph.planewave_linear_128()
+    line, st = measure_rf(ctx, "planewave-linear-128", w, "plain", 5, 2, cpu_seconds=2.0, e2e=False)
+    st["plan"].close()
+    out["planewave-linear-128"] = compact(line)
+    out["planewave-linear-128-grad"] = compact(measure_grad(ctx, 5, 2))
+    out["ragged-batch-x0.05"] = compact(measure_batch(ctx, 256, 0.05, "tc_f16", 2, 1))
+    w = WORKLOADS[DEFAULT_WORKLOAD]()
+    line, st = measure_rf(ctx, DEFAULT_WORKLOAD, w, "tc_bf16", 5, 2, e2e=False,
+                          oracle_ref=headline_ref)
+    st["plan"].close()
+    out[DEFAULT_WORKLOAD + "-bf16"] = compact(line)
+    out["seconds"] = time.time() - t0
+    return out
+
+
+def run_ours(args, rank, ws, local):
+    ctx = Ctx(local, ws)
+    tuning = dict(kv.split("=") for kv in args.tune) if args.tune else None
+    tuning = {k: int(v) for k, v in tuning.items()} if tuning else None
+    if args.workload == "ragged-batch":
+        line = measure_batch(ctx, args.n_sims, args.scale, args.path or "tc_f16", args.steps,
+                             args.warmup)
+    elif args.workload == "planewave-linear-128-grad":
+        line = measure_grad(ctx, args.steps, args.warmup, args.path or "plain", args.n_scat,
+                            accuracy=not args.no_cpu_baseline)
+    elif args.workload == "pfield-l11-5v":
+        line = measure_pfield(ctx, args.steps, args.warmup, accuracy=not args.no_cpu_baseline)
+    else:
+        w = WORKLOADS[args.workload](**({"n_scat": args.n_scat} if args.n_scat else {}))
+        path = args.path or DEFAULT_PATH[args.workload]
+        line, st = measure_rf(ctx, args.workload, w, path, args.steps, args.warmup,
+                              cpu_seconds=None if args.no_cpu_baseline else args.cpu_seconds,
+                              tuning=tuning)
+        if path != "plain" and not args.no_plain_compare:
+            pc = measure_plain_compare(ctx, w, st, max(5, min(args.steps, 10)))
+            pc["speedup_of_this_path"] = pc["ms_per_step_median"] / line["ms_per_step_median"]
+            line["plain_f32_same_workload"] = pc
+        st["plan"].close()
+        if (args.workload == DEFAULT_WORKLOAD and not args.n_scat and ws == 1 and not tuning
+                and not args.no_other_configs):
+            line["other_configs"] = other_configs(ctx, st["ref"])
     if rank == 0:
         print(json.dumps(line), flush=True)
-    plan.close()
 
 
 def main():
@@ -706,6 +748,10 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain-compare", action="store_true")
+    ap.add_argument("--no-other-configs", action="store_true",
+                    help="headline workload only (no sub-records of the other workloads)")
+    ap.add_argument("--tune", nargs="*", default=None,
+                    help="tensor-core tuning overrides, e.g. delta_table=0 pair=1")
     ap.add_argument("--n-scat", type=int, default=0,
                     help="override the workload's scatterer count (profiling of small cases)")
     ap.add_argument("--n-sims", type=int, default=256, help="ragged-batch: simulations")
@@ -714,12 +760,6 @@ def main():
     rank, ws, local = dist_init()
     if args.impl == "reference":
         run_reference(args, rank, ws)
-    elif args.workload == "ragged-batch":
-        run_batch_bench(args, rank, ws, local)
-    elif args.workload == "planewave-linear-128-grad":
-        run_grad_bench(args, rank, ws, local)
-    elif args.workload == "pfield-l11-5v":
-        run_pfield_bench(args, rank, ws, local)
     else:
         run_ours(args, rank, ws, local)
     if ws > 1:
