@@ -40,10 +40,12 @@ __device__ __forceinline__ uint16_t h16(float v) {
     return __half_as_ushort(__float2half_rn(v));
 }
 
-// shared memory a unit needs after the header
-size_t unit_smem(int Np, int nN, int nbuf, int M, int tab_n) {
+// shared memory a unit needs after the header (split BF16: the tile's remainders in a
+// second buffer, B1 and B2 doubled)
+size_t unit_smem(int Np, int nN, int nbuf, int M, int tab_n, bool split) {
     const size_t a = (size_t)kSB * 2 * Np * 2;
-    return nbuf * a + (size_t)nN * 2 * Np * 2 + (size_t)nN * 256 * 2
+    const size_t ops = split ? 2 : 1;
+    return (split ? 2 : nbuf) * a + ops * ((size_t)nN * 2 * Np * 2 + (size_t)nN * 256 * 2)
          + sizeof(float4) * kSB + sizeof(float4) * M + 2 * sizeof(float4) * tab_n;
 }
 }  // namespace
@@ -51,12 +53,14 @@ size_t unit_smem(int Np, int nN, int nbuf, int M, int tab_n) {
 // B1 images of one simulation: per kept bin and transmit group g, the nN x 2Np K-major
 // operand of the transmit GEMM for transmits g TG .. g TG + TG - 1 (image [k][g]),
 //   row 2t: (Re C, -Im C), row 2t+1: (Im C, Re C), C = W exp(i 2 pi frac(q df dtau)).
+// BF16 images are split: the BF16 leading parts, then the BF16 remainders C - hi.
 template <bool BF16>
 __global__ void k_tc_weights(int T, int G, int TG, int N, int Np, int nN, int nq, int q_lo,
                              double df, const float *__restrict__ delays,
                              const float *__restrict__ apod, uint16_t *__restrict__ img) {
     const int K = 2 * Np;
     const int64_t per_img = (int64_t)nN * K;
+    constexpr int kOps = BF16 ? 2 : 1;
     const int64_t total = per_img * G * nq;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -78,7 +82,9 @@ __global__ void k_tc_weights(int T, int G, int TG, int N, int Np, int nN, int nq
             bool first_half = kk < Np;
             v = (n & 1) ? (first_half ? ci : cr) : (first_half ? cr : -ci);
         }
-        img[(size_t)kg * per_img + tc::kmajor_offset(n, kk, K) / 2] = h16<BF16>(v);
+        const size_t o = (size_t)kg * kOps * per_img + tc::kmajor_offset(n, kk, K) / 2;
+        img[o] = h16<BF16>(v);
+        if (BF16) img[o + per_img] = h16<true>(v - __bfloat162float(__float2bfloat16_rn(v)));
     }
 }
 
@@ -92,6 +98,11 @@ TcShape tc_shape(const simus_plan *p, int T, int64_t S, double work_share, int i
     g.mh = g.Np > 128 ? 2 : 1;
     const size_t limit = 227 * 1024 - kHeader - 1024;
     const int tab_full = (p->delta_table && p->d_dtab) ? p->gc.tab_n : 0;
+    // BF16 operands are split into leading parts and remainders: one logical tile buffer
+    // (the remainders take the second), stash slots of 2 Np columns, at most two bins per
+    // pass (the packed leading parts and remainders of three bins exceed the registers)
+    const bool split = p->path == SIMUS_PATH_TC_BF16;
+    const int ops = split ? 2 : 1;
     // Bins per generation pass (sharing one geometry setup) and shared-memory tile
     // buffers, most sharing first: (3, 2), (3, 1), (2, 2), (2, 1), (1, 1); bins past the
     // buffers wait in tensor-memory stash slots of Np columns.  At most two transmit
@@ -101,18 +112,23 @@ TcShape tc_shape(const simus_plan *p, int T, int64_t S, double work_share, int i
     for (int mi = 0; mi < 5 && !g.ok; ++mi) {
         const int per = kModes[mi][0], nbuf = kModes[mi][1];
         if (per > p->pair_mode + 1) continue;
-        const int stash = (per - nbuf) * g.Np;       // tensor-memory columns of the stash
+        if (split && (nbuf != 1 || per > 2)) continue;
+        const int stash = (per - nbuf) * g.Np * ops;   // tensor-memory columns of the stash
         for (int tb = 0; tb < 2 && !g.ok; ++tb) {
             const int tab_n = tb ? 0 : tab_full;
             if (tb && !tab_full) break;
-            for (int TG = std::min(T, 120); TG >= 1 && !g.ok; TG = (TG > 8 ? TG - 8 : TG - 1)) {
+            // transmit-group sizes, largest first: FP16 steps down by 8; split BF16 (whose
+            // operands fill shared memory at smaller groups) takes the largest size of
+            // each group count, ceil(T / G)
+            for (int TG = std::min(T, 120), G0 = 1; TG >= 1 && !g.ok;
+                 TG = split ? (G0 < T ? (T + G0) / (G0 + 1) : 0) : (TG > 8 ? TG - 8 : TG - 1), ++G0) {
                 const int nN = ((2 * TG + 15) / 16) * 16;
                 const int G = (T + TG - 1) / TG;
                 if (per > 1 && G > 2) break;
                 if (nN + stash > 512) continue;
                 const int qb = (512 - nN - stash) / (nN * G * g.mh);
                 if (qb < per) continue;
-                const size_t sm = unit_smem(g.Np, nN, nbuf, p->M, tab_n);
+                const size_t sm = unit_smem(g.Np, nN, nbuf, p->M, tab_n, split);
                 if (sm > limit) continue;
                 g.ok = true;
                 g.TG = TG; g.nN = nN; g.pair = per - 1; g.nbuf = nbuf; g.n_groups = G;
@@ -150,7 +166,7 @@ TcShape tc_shape(const simus_plan *p, int T, int64_t S, double work_share, int i
     }
     g.tiles_per_chunk = (int)((g.n_tiles + chunks - 1) / chunks);
     g.n_chunks = (int)((g.n_tiles + g.tiles_per_chunk - 1) / g.tiles_per_chunk);
-    g.b1_bytes = (size_t)p->nq * g.n_groups * g.nN * 2 * g.Np * 2;
+    g.b1_bytes = (size_t)p->nq * g.n_groups * g.nN * 2 * g.Np * 2 * ops;
     return g;
 }
 
@@ -191,10 +207,11 @@ int launch_tc_units(const TcUnit *h_units, const TcUnit *d_units, int n_units, i
         int rc = check_cuda(cudaGetLastError(), "k_tc_weights launch");
         if (rc) return rc;
     }
-    const TcKernelFn kern = has_y ? (sinc_mode == 1 ? tc_kernel_y1_narrow(linear) : tc_kernel_y1_wide(linear))
-                                  : (sinc_mode == 1 ? tc_kernel_y0_narrow(linear)
-                                                    : (sinc_mode == 2 ? tc_kernel_y0_mid(linear)
-                                                                      : tc_kernel_y0_wide(linear)));
+    // BF16 operands always go through the split (leading part + remainder) kernels
+    const TcKernelFn kern = has_y ? (sinc_mode == 1 ? tc_kernel_y1_narrow(linear, bf16) : tc_kernel_y1_wide(linear, bf16))
+                                  : (sinc_mode == 1 ? tc_kernel_y0_narrow(linear, bf16)
+                                                    : (sinc_mode == 2 ? tc_kernel_y0_mid(linear, bf16)
+                                                                      : tc_kernel_y0_wide(linear, bf16)));
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return check_cuda(e, "k_tc_rf smem attribute");
     const int grid = (int)std::min<int64_t>(n_items, num_sms);

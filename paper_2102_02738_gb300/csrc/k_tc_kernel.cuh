@@ -28,6 +28,18 @@ __device__ __forceinline__ uint32_t h16x2(bool bf16, float lo, float hi) {
     return *reinterpret_cast<const uint32_t *>(&v);
 }
 
+// Two FP32 values as BF16 leading parts (hi) and BF16 remainders (rem = v - hi, rounded):
+// hi + rem carries 16 significant bits, and a product of two such pairs formed as
+// hi hi' + hi rem' + rem hi' misses only rem rem' (relative 2^-16) and the remainders'
+// own roundings (2^-17 each).
+__device__ __forceinline__ void bf16_split2(float a, float b, uint32_t &hi, uint32_t &rem) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    const float2 hf = __bfloat1622float2(h);
+    const __nv_bfloat162 r = __floats2bfloat162_rn(a - hf.x, b - hf.y);
+    hi = *reinterpret_cast<const uint32_t *>(&h);
+    rem = *reinterpret_cast<const uint32_t *>(&r);
+}
+
 
 // Sub-element sums (Eq. 33) of the Green's terms of elements e0 and e0 + 1 for one
 // scatterer at the NB consecutive bins qA, qA + 1, ...: two independent evaluation chains
@@ -159,41 +171,57 @@ __device__ __forceinline__ void gen_two(const GreenConst &gc, const float4 *sub,
 // to a tensor-memory stash slot (slot i at columns stash + i Np: row s in lane s, Re of the
 // 8 elements packed in columns 4 eg .. + 3, Im at Np/2 + 4 eg) until a buffer is free.
 // The lane rule holds by construction: item it has s = it mod 128 = 32 (warp mod 4) + lane.
-template <int NB, int NBUF, bool TAB, bool HAS_Y, int SINC, bool LINEAR>
+// Split BF16 (split, one logical buffer, at most two bins per pass): bin 0's leading parts
+// go to A0 and its remainders to A1; a stash slot is 2 Np columns, the remainders at + Np.
+template <int NB, int NBUF, bool TAB, bool HAS_Y, int SINC, bool LINEAR, bool SPLIT>
 __device__ __forceinline__ void gen_tiles(const GreenConst &gc, const float4 *sub,
                                           const float4 *tabs, const float4 *sc, int Np,
                                           float qA, unsigned char *A0, unsigned char *A1,
                                           uint32_t stash, bool bf16, int tid) {
     constexpr int nbuf = NBUF < NB ? NBUF : NB;
+    constexpr bool split = NB < 3 && SPLIT;       // (three-bin passes are never split)
     const int K1 = 2 * Np;
     const int n_groups = Np >> 3;
+    const uint32_t sstride = split ? 2u * Np : (uint32_t)Np;
     for (int it = tid; it < kSB * n_groups; it += kThreads) {
         const int s = it & (kSB - 1), eg = it >> 7;
         const float4 ps = sc[s];
-        uint32_t pk[NB][2][4];
+        uint32_t pk[NB][2][4], pr[NB][2][4];
 #pragma unroll
         for (int jp = 0; jp < 4; ++jp) {
             float o[2][NB][2];
             gen_two<NB, TAB, HAS_Y, SINC, LINEAR>(gc, sub, tabs, ps, eg * 8 + 2 * jp, qA, o);
 #pragma unroll
             for (int b = 0; b < NB; ++b) {
-                pk[b][0][jp] = h16x2(bf16, o[0][b][0], o[1][b][0]);
-                pk[b][1][jp] = h16x2(bf16, o[0][b][1], o[1][b][1]);
+                if (split) {
+                    bf16_split2(o[0][b][0], o[1][b][0], pk[b][0][jp], pr[b][0][jp]);
+                    bf16_split2(o[0][b][1], o[1][b][1], pk[b][1][jp], pr[b][1][jp]);
+                } else {
+                    pk[b][0][jp] = h16x2(bf16, o[0][b][0], o[1][b][0]);
+                    pk[b][1][jp] = h16x2(bf16, o[0][b][1], o[1][b][1]);
+                }
             }
         }
         const uint32_t ta = stash + ((uint32_t)(s & ~31) << 16) + 4u * eg;
+        const uint32_t o_re = tc::kmajor_offset(s, eg * 8, K1), o_im = tc::kmajor_offset(s, Np + eg * 8, K1);
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
             if (b < nbuf) {
                 unsigned char *A = b ? A1 : A0;
-                *reinterpret_cast<uint4 *>(A + tc::kmajor_offset(s, eg * 8, K1)) =
-                    make_uint4(pk[b][0][0], pk[b][0][1], pk[b][0][2], pk[b][0][3]);
-                *reinterpret_cast<uint4 *>(A + tc::kmajor_offset(s, Np + eg * 8, K1)) =
-                    make_uint4(pk[b][1][0], pk[b][1][1], pk[b][1][2], pk[b][1][3]);
+                *reinterpret_cast<uint4 *>(A + o_re) = make_uint4(pk[b][0][0], pk[b][0][1], pk[b][0][2], pk[b][0][3]);
+                *reinterpret_cast<uint4 *>(A + o_im) = make_uint4(pk[b][1][0], pk[b][1][1], pk[b][1][2], pk[b][1][3]);
+                if (split) {
+                    *reinterpret_cast<uint4 *>(A1 + o_re) = make_uint4(pr[b][0][0], pr[b][0][1], pr[b][0][2], pr[b][0][3]);
+                    *reinterpret_cast<uint4 *>(A1 + o_im) = make_uint4(pr[b][1][0], pr[b][1][1], pr[b][1][2], pr[b][1][3]);
+                }
             } else {
-                const uint32_t ts = ta + (uint32_t)((b - nbuf) * Np);
+                const uint32_t ts = ta + (uint32_t)(b - nbuf) * sstride;
                 tc::tmem_st4(ts, pk[b][0][0], pk[b][0][1], pk[b][0][2], pk[b][0][3]);
                 tc::tmem_st4(ts + (uint32_t)(Np >> 1), pk[b][1][0], pk[b][1][1], pk[b][1][2], pk[b][1][3]);
+                if (split) {
+                    tc::tmem_st4(ts + (uint32_t)Np, pr[b][0][0], pr[b][0][1], pr[b][0][2], pr[b][0][3]);
+                    tc::tmem_st4(ts + (uint32_t)(Np + (Np >> 1)), pr[b][1][0], pr[b][1][1], pr[b][1][2], pr[b][1][3]);
+                }
             }
         }
     }
@@ -201,25 +229,37 @@ __device__ __forceinline__ void gen_tiles(const GreenConst &gc, const float4 *su
 }
 
 // Move a stashed bin from tensor memory into tile buffer A (same item-to-thread map as
-// gen_tiles, so every thread reads back the lanes and columns it wrote).
-__device__ __forceinline__ void unstash_tile(int Np, unsigned char *A, uint32_t slot, int tid) {
+// gen_tiles, so every thread reads back the lanes and columns it wrote); split BF16: the
+// remainders (slot + Np) into Ar.
+__device__ __forceinline__ void unstash_tile(int Np, unsigned char *A, unsigned char *Ar, bool split,
+                                             uint32_t slot, int tid) {
     const int K1 = 2 * Np;
     const int n_groups = Np >> 3;
     for (int it = tid; it < kSB * n_groups; it += kThreads) {
         const int s = it & (kSB - 1), eg = it >> 7;
         const uint32_t ta = slot + ((uint32_t)(s & ~31) << 16) + 4u * eg;
+        const uint32_t o_re = tc::kmajor_offset(s, eg * 8, K1), o_im = tc::kmajor_offset(s, Np + eg * 8, K1);
         uint32_t re[4], im[4];
         tc::tmem_ld4(ta, re);
         tc::tmem_ld4(ta + (uint32_t)(Np >> 1), im);
         tc::tmem_wait_ld();
-        *reinterpret_cast<uint4 *>(A + tc::kmajor_offset(s, eg * 8, K1)) = make_uint4(re[0], re[1], re[2], re[3]);
-        *reinterpret_cast<uint4 *>(A + tc::kmajor_offset(s, Np + eg * 8, K1)) = make_uint4(im[0], im[1], im[2], im[3]);
+        *reinterpret_cast<uint4 *>(A + o_re) = make_uint4(re[0], re[1], re[2], re[3]);
+        *reinterpret_cast<uint4 *>(A + o_im) = make_uint4(im[0], im[1], im[2], im[3]);
+        if (split) {
+            tc::tmem_ld4(ta + (uint32_t)Np, re);
+            tc::tmem_ld4(ta + (uint32_t)(Np + (Np >> 1)), im);
+            tc::tmem_wait_ld();
+            *reinterpret_cast<uint4 *>(Ar + o_re) = make_uint4(re[0], re[1], re[2], re[3]);
+            *reinterpret_cast<uint4 *>(Ar + o_im) = make_uint4(im[0], im[1], im[2], im[3]);
+        }
     }
 }
 
 }  // namespace
 
-template <bool HAS_Y, int SINC, bool LINEAR>
+// SPLIT: BF16 operands as leading parts + remainders, three products per GEMM (bf16
+// must then be 1); otherwise FP16 (bf16 = 0) or plain BF16 (bf16 = 1) operands.
+template <bool HAS_Y, int SINC, bool LINEAR, bool SPLIT>
 __global__ void __launch_bounds__(kThreads, 1)
 k_tc_rf(const TcUnit *__restrict__ units, int n_units, int64_t n_items, int *counter, int *err,
         int bf16) {
@@ -301,11 +341,16 @@ k_tc_rf(const TcUnit *__restrict__ units, int n_units, int64_t n_items, int *cou
         const int G = U.G, T = U.T, nbuf = U.nbuf;
         const int K1 = 2 * Np;
         const size_t abytes = (size_t)kSB * K1 * 2;
+        // split BF16: every operand as leading part + remainder; the remainders of the
+        // tile in A1, of B1 and B2 right after their leading parts
+        constexpr bool split = SPLIT;
+        const int nops = split ? 2 : 1;
         unsigned char *A0 = dyn;
-        unsigned char *A1 = A0 + (nbuf == 2 ? abytes : 0);
-        unsigned char *B1 = A0 + nbuf * abytes;
-        unsigned char *B2 = B1 + (size_t)nN * K1 * 2;
-        float4 *sc = reinterpret_cast<float4 *>(B2 + (size_t)nN * 256 * 2);
+        unsigned char *A1 = A0 + (nbuf == 2 || split ? abytes : 0);
+        unsigned char *B1 = A0 + (split ? 2 : nbuf) * abytes;
+        const uint32_t b1_part = (uint32_t)nN * K1 * 2, b2_part = (uint32_t)nN * 256 * 2;
+        unsigned char *B2 = B1 + (size_t)nops * b1_part;
+        float4 *sc = reinterpret_cast<float4 *>(B2 + (size_t)nops * b2_part);
         float4 *sub = sc + kSB;                                            // compact records
         float4 *tabs = sub + M;                                            // delta table
         const bool use_tab = !HAS_Y && gc.tab_n > 0;
@@ -313,7 +358,7 @@ k_tc_rf(const TcUnit *__restrict__ units, int n_units, int64_t n_items, int *cou
         const uint32_t b1s = tc::smem_u32(B1), b2s = tc::smem_u32(B2);
         const uint32_t idesc1 = tc::idesc_f16(128, nN, bf16 != 0);
         const uint32_t idesc2 = idesc1 | (1u << 15) | (1u << 16);   // A and B MN-major
-        const uint32_t b1_bytes = (uint32_t)nN * K1 * 2;
+        const uint32_t b1_bytes = nops * b1_part;
         if (ui != cur_unit) {
             for (int i = tid; i < M; i += kThreads) sub[i] = compact_sub(U.sub[i], LINEAR);
             if (use_tab)
@@ -324,7 +369,7 @@ k_tc_rf(const TcUnit *__restrict__ units, int n_units, int64_t n_items, int *cou
         auto issue_b1 = [&](int k, int g) {   // weights of bin k, transmit group g
             if (tid == 0) {
                 tc::mbar_arrive_expect_tx(mbar_b1, b1_bytes);
-                tc::bulk_g2s(b1s, U.b1img + ((size_t)k * G + g) * nN * K1, b1_bytes, mbar_b1);
+                tc::bulk_g2s(b1s, U.b1img + ((size_t)k * G + g) * nops * nN * K1, b1_bytes, mbar_b1);
                 b1_inflight = true;
             }
         };
@@ -336,6 +381,7 @@ k_tc_rf(const TcUnit *__restrict__ units, int n_units, int64_t n_items, int *cou
         const int64_t tile1 = std::min<int64_t>(tile0 + U.tiles_per_chunk, U.n_tiles);
         const int step = pair + 1;                        // bins per generation pass
         const uint32_t stash = tmem + (uint32_t)(nN * (1 + QB * G * mh));   // stash slots of Np columns
+        const uint32_t sstride = (uint32_t)(nops * Np);                     // (2 Np when split)
         for (int64_t tile = tile0; tile < tile1 && !aborted; ++tile) {
             for (int bp = 0; bp < QB && !aborted; bp += step) {
                 const int nb = min(step, QB - bp);
@@ -359,8 +405,8 @@ k_tc_rf(const TcUnit *__restrict__ units, int n_units, int64_t n_items, int *cou
                 const bool tab = !HAS_Y && use_tab;
 #define SIMUS_GEN(NB_, NBUF_)                                                                     \
     do {                                                                                          \
-        if (tab) gen_tiles<NB_, NBUF_, !HAS_Y, HAS_Y, SINC, LINEAR>(gc, sub, tabs, sc, Np, qA, A0, A1, stash, bf16 != 0, tid); \
-        else gen_tiles<NB_, NBUF_, false, HAS_Y, SINC, LINEAR>(gc, sub, tabs, sc, Np, qA, A0, A1, stash, bf16 != 0, tid);     \
+        if (tab) gen_tiles<NB_, NBUF_, !HAS_Y, HAS_Y, SINC, LINEAR, SPLIT>(gc, sub, tabs, sc, Np, qA, A0, A1, stash, bf16 != 0, tid); \
+        else gen_tiles<NB_, NBUF_, false, HAS_Y, SINC, LINEAR, SPLIT>(gc, sub, tabs, sc, Np, qA, A0, A1, stash, bf16 != 0, tid);     \
     } while (0)
                 if (nb == 3) {
                     if (nbuf == 2) SIMUS_GEN(3, 2); else SIMUS_GEN(3, 1);
@@ -391,7 +437,7 @@ k_tc_rf(const TcUnit *__restrict__ units, int n_units, int64_t n_items, int *cou
                             ph2 ^= 1;
                             pending2 = false;
                         }
-                        unstash_tile(Np, buf ? A1 : A0, stash + (uint32_t)((bi_ - nbuf) * Np), tid);
+                        unstash_tile(Np, buf ? A1 : A0, A1, split, stash + (uint32_t)(bi_ - nbuf) * sstride, tid);
                         tc::fence_proxy_async_smem();
                         tc::fence_before_sync();
                         __syncthreads();
@@ -410,10 +456,23 @@ k_tc_rf(const TcUnit *__restrict__ units, int n_units, int64_t n_items, int *cou
                             const uint64_t ad0 = tc::smem_desc(abase, 128, 16 * K1);
                             const uint64_t bd0 = tc::smem_desc(b1s, 128, 16 * K1);
                             const int nk = K1 / 16;
+                            if (!split) {
 #pragma unroll
-                            for (int j = 0; j < 32; ++j) {
-                                if (j >= nk) break;
-                                tc::mma_f16(tmem, ad0 + 16ull * j, bd0 + 16ull * j, idesc1, j > 0 ? 1u : 0u);
+                                for (int j = 0; j < 32; ++j) {
+                                    if (j >= nk) break;
+                                    tc::mma_f16(tmem, ad0 + 16ull * j, bd0 + 16ull * j, idesc1, j > 0 ? 1u : 0u);
+                                }
+                            } else {
+                                // (A + A_r)(B + B_r) without A_r B_r: three products
+                                const uint64_t adr = tc::smem_desc(abuf1, 128, 16 * K1);
+                                const uint64_t bdr = tc::smem_desc(b1s + b1_part, 128, 16 * K1);
+#pragma unroll
+                                for (int j = 0; j < 32; ++j) {
+                                    if (j >= nk) break;
+                                    tc::mma_f16(tmem, ad0 + 16ull * j, bd0 + 16ull * j, idesc1, j > 0 ? 1u : 0u);
+                                    tc::mma_f16(tmem, ad0 + 16ull * j, bdr + 16ull * j, idesc1, 1u);
+                                    tc::mma_f16(tmem, adr + 16ull * j, bd0 + 16ull * j, idesc1, 1u);
+                                }
                             }
                             tc::mma_commit(mbar1);
                         }
@@ -442,14 +501,19 @@ k_tc_rf(const TcUnit *__restrict__ units, int n_units, int64_t n_items, int *cou
                         for (int c0 = cc * 16; c0 < nN; c0 += 64) {
                             float v[16];
                             tc::tmem_ld16(tmem + ((uint32_t)(sp * 32) << 16) + (uint32_t)c0, v);
-                            uint32_t w0[8], w1[8];
+                            uint32_t w0[8], w1[8], r0[8], r1[8];
 #pragma unroll
                             for (int i = 0; i < 8; ++i) {
                                 const int t = (c0 >> 1) + i;
                                 float pr = 0.f, pi = 0.f;
                                 if (t < TGg) { pr = R * v[2 * i]; pi = R * v[2 * i + 1]; }
-                                w0[i] = h16x2(bf16 != 0, pr, pi);
-                                w1[i] = h16x2(bf16 != 0, -pi, pr);
+                                if (split) {
+                                    bf16_split2(pr, pi, w0[i], r0[i]);
+                                    bf16_split2(-pi, pr, w1[i], r1[i]);
+                                } else {
+                                    w0[i] = h16x2(bf16 != 0, pr, pi);
+                                    w1[i] = h16x2(bf16 != 0, -pi, pr);
+                                }
                             }
                             const uint32_t nrow = (uint32_t)(nN >> 3);
                             unsigned char *q0 = B2 + ((((uint32_t)(s >> 3) * nrow + (uint32_t)(c0 >> 3)) << 7) + ((s & 7) << 4));
@@ -458,6 +522,12 @@ k_tc_rf(const TcUnit *__restrict__ units, int n_units, int64_t n_items, int *cou
                             *reinterpret_cast<uint4 *>(q0 + 128) = make_uint4(w0[4], w0[5], w0[6], w0[7]);
                             *reinterpret_cast<uint4 *>(q1) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
                             *reinterpret_cast<uint4 *>(q1 + 128) = make_uint4(w1[4], w1[5], w1[6], w1[7]);
+                            if (split) {                               // remainders at B2 + b2_part
+                                *reinterpret_cast<uint4 *>(q0 + b2_part) = make_uint4(r0[0], r0[1], r0[2], r0[3]);
+                                *reinterpret_cast<uint4 *>(q0 + b2_part + 128) = make_uint4(r0[4], r0[5], r0[6], r0[7]);
+                                *reinterpret_cast<uint4 *>(q1 + b2_part) = make_uint4(r1[0], r1[1], r1[2], r1[3]);
+                                *reinterpret_cast<uint4 *>(q1 + b2_part + 128) = make_uint4(r1[4], r1[5], r1[6], r1[7]);
+                            }
                         }
                     }
                     tc::fence_proxy_async_smem();
@@ -477,13 +547,25 @@ k_tc_rf(const TcUnit *__restrict__ units, int n_units, int64_t n_items, int *cou
                         const uint64_t sa = (uint64_t)(2 * K1), sim = (uint64_t)Np, sb = (uint64_t)(2 * nN);
                         const uint32_t acc0 = tile > tile0 ? 1u : 0u;
                         const uint64_t bd0 = tc::smem_desc(b2s, 16 * nN, 128);
+                        const uint64_t bdr = tc::smem_desc(b2s + b2_part, 16 * nN, 128);
                         for (int h = 0; h < mh; ++h) {
                             const uint32_t d2 = tmem + (uint32_t)(nN * (1 + ((bp + bi_) * G + g) * mh + h));
                             const uint64_t ad0 = tc::smem_desc(abase + (uint32_t)(h * 16 * 128), 16 * K1, 128);
+                            if (!split) {
 #pragma unroll
-                            for (int j = 0; j < 16; ++j)
-                                tc::mma_f16(d2, ad0 + (uint64_t)(j & 7) * sa + (uint64_t)(j >> 3) * sim,
-                                            bd0 + (uint64_t)j * sb, idesc2, j > 0 ? 1u : acc0);
+                                for (int j = 0; j < 16; ++j)
+                                    tc::mma_f16(d2, ad0 + (uint64_t)(j & 7) * sa + (uint64_t)(j >> 3) * sim,
+                                                bd0 + (uint64_t)j * sb, idesc2, j > 0 ? 1u : acc0);
+                            } else {
+                                const uint64_t adr = tc::smem_desc(abuf1 + (uint32_t)(h * 16 * 128), 16 * K1, 128);
+#pragma unroll
+                                for (int j = 0; j < 16; ++j) {
+                                    const uint64_t ka = (uint64_t)(j & 7) * sa + (uint64_t)(j >> 3) * sim;
+                                    tc::mma_f16(d2, ad0 + ka, bd0 + (uint64_t)j * sb, idesc2, j > 0 ? 1u : acc0);
+                                    tc::mma_f16(d2, ad0 + ka, bdr + (uint64_t)j * sb, idesc2, 1u);
+                                    tc::mma_f16(d2, adr + ka, bd0 + (uint64_t)j * sb, idesc2, 1u);
+                                }
+                            }
                         }
                         tc::mma_commit(mbar2);
                     }
@@ -539,11 +621,17 @@ k_tc_rf(const TcUnit *__restrict__ units, int n_units, int64_t n_items, int *cou
 
 
 using TcKernelFn = void (*)(const TcUnit *, int, int64_t, int *, int *, int);
-// Instantiations, one translation unit each (see k_tc_rf_*.cu).
-TcKernelFn tc_kernel_y0_narrow(bool linear);
-TcKernelFn tc_kernel_y0_mid(bool linear);
-TcKernelFn tc_kernel_y0_wide(bool linear);
-TcKernelFn tc_kernel_y1_narrow(bool linear);
-TcKernelFn tc_kernel_y1_wide(bool linear);
+// Instantiations, one translation unit each (see k_tc_rf_*.cu); split: the split-BF16
+// kernels (k_tc_rf_bf16_*.cu).
+TcKernelFn tc_kernel_y0_narrow(bool linear, bool split);
+TcKernelFn tc_kernel_y0_mid(bool linear, bool split);
+TcKernelFn tc_kernel_y0_wide(bool linear, bool split);
+TcKernelFn tc_kernel_y1_narrow(bool linear, bool split);
+TcKernelFn tc_kernel_y1_wide(bool linear, bool split);
+TcKernelFn tc_kernel_bf16_y0_narrow(bool linear);
+TcKernelFn tc_kernel_bf16_y0_mid(bool linear);
+TcKernelFn tc_kernel_bf16_y0_wide(bool linear);
+TcKernelFn tc_kernel_bf16_y1_narrow(bool linear);
+TcKernelFn tc_kernel_bf16_y1_wide(bool linear);
 
 }  // namespace simus

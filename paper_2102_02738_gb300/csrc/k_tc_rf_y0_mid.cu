@@ -3,7 +3,8 @@
 #include "k_tc_kernel.cuh"
 
 namespace simus {
-TcKernelFn tc_kernel_y0_mid(bool linear) {
-    return linear ? k_tc_rf<false, 2, true> : k_tc_rf<false, 2, false>;
+TcKernelFn tc_kernel_y0_mid(bool linear, bool split) {
+    if (split) return tc_kernel_bf16_y0_mid(linear);
+    return linear ? k_tc_rf<false, 2, true, false> : k_tc_rf<false, 2, false, false>;
 }
 }  // namespace simus

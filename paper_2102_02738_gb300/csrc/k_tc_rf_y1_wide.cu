@@ -3,7 +3,8 @@
 #include "k_tc_kernel.cuh"
 
 namespace simus {
-TcKernelFn tc_kernel_y1_wide(bool linear) {
-    return linear ? k_tc_rf<true, 0, true> : k_tc_rf<true, 0, false>;
+TcKernelFn tc_kernel_y1_wide(bool linear, bool split) {
+    if (split) return tc_kernel_bf16_y1_wide(linear);
+    return linear ? k_tc_rf<true, 0, true, false> : k_tc_rf<true, 0, false, false>;
 }
 }  // namespace simus

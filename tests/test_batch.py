@@ -89,6 +89,14 @@ def test_ragged_batch_tc_matches_oracle(S, oracle):
         assert rel_l2(rf.cpu().numpy(), oracle_rf(oracle, w)) <= TOL_TC, w.name
 
 
+def test_ragged_batch_bf16_matches_oracle(S, oracle):
+    sims = [w for w in ragged(n_sims=10, seed=1006) if w.cfg["n_elements"] <= 176][:5]
+    plans, _, _, rfs = run_batch(S, sims, "tc_bf16")
+    S.simus_plan_check(plans[0].handle)
+    for w, rf in zip(sims, rfs):
+        assert rel_l2(rf.cpu().numpy(), oracle_rf(oracle, w)) <= TOL_TC, w.name
+
+
 def test_ragged_batch_plain_matches_oracle(S, oracle):
     sims = ragged(n_sims=3)
     _, _, _, rfs = run_batch(S, sims, "plain")
