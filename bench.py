@@ -46,7 +46,7 @@ NCU_TRAFFIC = {("diverging-convex-128", "tc_f16", 100000): 51.287040e6 + 222.054
 INST_PER_TERM = {("diverging-convex-128", "tc_f16", 100000): 4.527e10 * 32 / (864 * 100000 * 256),
                  ("planewave-linear-128", "plain", 20003): 1.633e10 * 32 / (763 * 20003 * 384)}
 # k_pfield on the 201 x 201 L11-5v grid (15 frequency chunks): DRAM read + write per launch
-PFIELD_TRAFFIC = 1.257114e6
+PFIELD_TRAFFIC = 1.250048e6
 METRIC = "Green's terms/s (freq x scatterer x sub-elem x tx)"
 WORKLOADS = {
     "planewave-linear-128": ph.planewave_linear_128,
