@@ -114,7 +114,7 @@ __device__ __forceinline__ void gen_two(const GreenConst &gc, const float4 *sub,
             const float q = qA + (float)b;
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
-                const float m = sinc_f<SINC>(q * P[c].xb);
+                const float m = sinc_short<SINC>(q * P[c].xb);
                 er[c][b] = zr[c] * m;
                 ei[c][b] = zi[c] * m;
                 if (b + 1 < NB) {
