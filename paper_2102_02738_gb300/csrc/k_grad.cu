@@ -101,14 +101,17 @@ k_adjoint_dft(const float *__restrict__ drf, int N, int n_chan, int nq, int q_lo
 // in different banks.  The sub-element records are held as two float4 planes indexed
 // [mu][e] (centroid; normal and rotated centroid), so that the threads of a warp, which
 // take consecutive elements, read consecutive 16-byte words instead of 32-byte records
-// nu apart.
-template <bool NARROW>
+// nu apart.  TAB: delta and d delta/dr from the plan's cubic pieces (staged after the other
+// tiles; the derivative of the piece in its variable times dx/dr), and the phase and
+// absorption of the tile's second bin from the first by one phasor step; points within
+// ~2 mm of a sub-element, outside the table, take the direct four-Gaussian form.
+template <bool NARROW, bool TAB>
 __global__ void __launch_bounds__(kGThreads, 1)
 k_grad(const GreenConst gc, const SubElem *__restrict__ sub_g, const float *__restrict__ xg,
        const float *__restrict__ zg, const float *__restrict__ rcg, int64_t S, int64_t chunk_len,
        int T, int SB, const float2 *__restrict__ cw, const float2 *__restrict__ lam,
        float *__restrict__ gpart /*[3][n_qtiles][S]*/, int n_qtiles,
-       float2 *__restrict__ bpart /*[n_chunks][T][nq][N]*/) {
+       float2 *__restrict__ bpart /*[n_chunks][T][nq][N]*/, const float4 *__restrict__ dtab) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int N = gc.N, nu = gc.nu, M = gc.M, nq = gc.nq, Nr = N + 1;
     const int tid = threadIdx.x;
@@ -125,12 +128,15 @@ k_grad(const GreenConst gc, const SubElem *__restrict__ sub_g, const float *__re
     float2 *RA = Gt + 3 * QB * SB * NrG;                            // [QB][SB][T]
     float *sg = reinterpret_cast<float *>(RA + QB * SB * T);        // [3][QB*SB*T]
     const int nit = QB * SB * T;
+    float4 *tabs = reinterpret_cast<float4 *>(sg + 3 * nit);        // [2 tab_n] (TAB)
 
     const int qt = blockIdx.x, chunk = blockIdx.y;
     const int k0 = qt * QB;
     const int64_t s_begin = (int64_t)chunk * chunk_len;
     const int64_t s_end = min(S, s_begin + chunk_len);
 
+    if (TAB)
+        for (int i = tid; i < 2 * gc.tab_n; i += kGThreads) tabs[i] = dtab[i];
     for (int i = tid; i < M; i += kGThreads) {          // global [e][mu] -> shared [mu][e]
         const float4 *r = reinterpret_cast<const float4 *>(sub_g + i);
         const int e = i / nu, mu = i - e * nu;
@@ -174,16 +180,64 @@ k_grad(const GreenConst gc, const SubElem *__restrict__ sub_g, const float *__re
                 reinterpret_cast<float4 *>(&se)[1] = subB[mu * N + e];
                 const PairSetup P = pair_setup<false>(gc, se, ps.x, 0.f, ps.z, q0);
                 const PairGrad Q = pair_grad(gc, se, ps.x, ps.z, P);
+                if (TAB) {
+                    // E = exp((i k - k_a) r) / r at q0 from the exact phase reduction, then
+                    // E <- E w, w = exp(-k_a r df / c) exp(2 pi i frac(u)) (as phase_run,
+                    // without the obliquity, which the derivative keeps apart)
+                    const float amp0 = gc.h * P.inv_r * ex2_a(-q0 * gc.att2 * P.rh);
+                    float sn, cs;
+                    sincos_a(6.283185307179586f * df_frac_mul(q0, P.u), sn, cs);
+                    float Er = amp0 * cs, Ei = amp0 * sn, wr = 0.f, wi = 0.f;
+                    if (QB > 1) {
+                        sincospif(2.0f * ((P.u.h - rintf(P.u.h)) + P.u.l), &sn, &cs);
+                        wr = P.mstep * cs;
+                        wi = P.mstep * sn;
+                    }
+                    const float kt = P.kap * gc.tab_inv_dx, t0 = gc.tab_x0 * gc.tab_inv_dx;
+                    const float dxdr = gc.tab_inv_dx * gc.kh * gc.h2 * Q.rr2;   // per bin
 #pragma unroll
-                for (int j = 0; j < QB; ++j) {
-                    const float q = q0 + (float)j;
-                    const float amp = (gc.two_d ? rsqrt_a(P.rh) : gc.h * P.inv_r) *
-                                      ex2_a(-q * gc.att2 * P.rh);
-                    float2 g, gx, gz;
-                    green_grad_term<NARROW>(gc, P, Q, q, amp, g, gx, gz);
-                    G[j].x += g.x; G[j].y += g.y;
-                    GX[j].x += gx.x; GX[j].y += gx.y;
-                    GZ[j].x += gz.x; GZ[j].y += gz.y;
+                    for (int j = 0; j < QB; ++j) {
+                        const float q = q0 + (float)j;
+                        const float tt = fmaf(q, kt, -t0);
+                        const float fl = floorf(fminf(fmaxf(tt, 0.0f), (float)gc.tab_n - 0.5f));
+                        const int i = (int)fl;
+                        const float u = tt - fl;
+                        float dr_, di_, ddr, ddi;
+                        if (u >= 0.0f && u <= 1.0f) {
+                            const float4 lo = tabs[2 * i], hi = tabs[2 * i + 1];
+                            const float2 d = cubic_piece(lo, hi, u);
+                            dr_ = d.x;
+                            di_ = d.y;
+                            // d/du of the piece: c1 + u (2 c2 + 3 c3 u)
+                            const float sc = q * dxdr;
+                            ddr = fmaf(u, fmaf(3.0f * u, hi.z, 2.0f * hi.x), lo.z) * sc;
+                            ddi = fmaf(u, fmaf(3.0f * u, hi.w, 2.0f * hi.y), lo.w) * sc;
+                        } else {
+                            delta_and_dr(gc, P, Q, q, dr_, di_, ddr, ddi);
+                        }
+                        float2 g, gx, gz;
+                        green_grad_assemble<NARROW>(gc, P, Q, q, Er, Ei, dr_, di_, ddr, ddi, g, gx, gz);
+                        G[j].x += g.x; G[j].y += g.y;
+                        GX[j].x += gx.x; GX[j].y += gx.y;
+                        GZ[j].x += gz.x; GZ[j].y += gz.y;
+                        if (j + 1 < QB) {
+                            const float nr = fmaf(Er, wr, -Ei * wi);
+                            Ei = fmaf(Er, wi, Ei * wr);
+                            Er = nr;
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < QB; ++j) {
+                        const float q = q0 + (float)j;
+                        const float amp = (gc.two_d ? rsqrt_a(P.rh) : gc.h * P.inv_r) *
+                                          ex2_a(-q * gc.att2 * P.rh);
+                        float2 g, gx, gz;
+                        green_grad_term<NARROW>(gc, P, Q, q, amp, g, gx, gz);
+                        G[j].x += g.x; G[j].y += g.y;
+                        GX[j].x += gx.x; GX[j].y += gx.y;
+                        GZ[j].x += gz.x; GZ[j].y += gz.y;
+                    }
                 }
             }
 #pragma unroll
@@ -362,13 +416,20 @@ GradGeom grad_geometry(const simus_plan *p, int T, int64_t S) {
     g.ok = (int64_t)T * p->N <= 2048;
     g.n_qtiles = (p->nq + kGQB - 1) / kGQB;
     const size_t Nr = (size_t)p->N + 1;
-    auto smem_for = [&](int SB) {
+    const int tab_full = (p->d_dtab && p->delta_table && !p->probe.two_d) ? p->gc.tab_n : 0;
+    auto smem_for = [&](int SB, int tab_n) {
         return sizeof(float4) * kGSBMax + sizeof(SubElem) * p->M
              + sizeof(float2) * (size_t)kGQB * T * Nr * 2 + sizeof(float2) * (size_t)kGQB * T * p->N
              + sizeof(float2) * (size_t)3 * kGQB * SB * grad_row(p->N, grad_ks(SB, T))
-             + sizeof(float2) * (size_t)kGQB * SB * T + sizeof(float) * 3 * kGQB * SB * T;
+             + sizeof(float2) * (size_t)kGQB * SB * T + sizeof(float) * 3 * kGQB * SB * T
+             + 2 * sizeof(float4) * (size_t)tab_n;
     };
-    g.SB = smem_for(kGSBMax) <= 227 * 1024 ? kGSBMax : 8;
+    // 16-scatterer groups with the delta table, else without it, else 8-scatterer groups
+    const size_t lim = 227 * 1024;
+    g.tab = tab_full > 0 && smem_for(kGSBMax, tab_full) <= lim;
+    g.SB = (g.tab || smem_for(kGSBMax, 0) <= lim) ? kGSBMax : 8;
+    if (g.SB == 8) g.tab = tab_full > 0 && smem_for(8, tab_full) <= lim;
+    const int tab_n = g.tab ? tab_full : 0;
     int64_t want = (int64_t)p->num_sms * 8;
     int64_t chunks = std::max<int64_t>(1, (want + g.n_qtiles - 1) / g.n_qtiles);
     chunks = std::min<int64_t>(chunks, std::max<int64_t>(1, S / (g.SB * 16)));
@@ -376,8 +437,8 @@ GradGeom grad_geometry(const simus_plan *p, int T, int64_t S) {
     len = ((len + g.SB - 1) / g.SB) * g.SB;
     g.chunk_len = std::max<int64_t>(len, g.SB);
     g.n_chunks = (int)((S + g.chunk_len - 1) / g.chunk_len);
-    g.smem = smem_for(g.SB);
-    g.ok = g.ok && g.smem <= 227 * 1024;
+    g.smem = smem_for(g.SB, tab_n);
+    g.ok = g.ok && g.smem <= lim;
     return g;
 }
 
@@ -392,12 +453,13 @@ int launch_adjoint_dft(const simus_plan *p, const float *drf, int T, float2 *lam
 
 int launch_grad(const simus_plan *p, const GradGeom &g, const simus_scat *sc, int T,
                 const float2 *cw, const float2 *lam, float *gpart, float2 *bpart, cudaStream_t st) {
-    auto kern = p->gc.narrow == 1 ? k_grad<true> : k_grad<false>;
+    auto kern = p->gc.narrow == 1 ? (g.tab ? k_grad<true, true> : k_grad<true, false>)
+                                  : (g.tab ? k_grad<false, true> : k_grad<false, false>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
     if (e != cudaSuccess) return check_cuda(e, "k_grad smem attribute");
     dim3 grid(g.n_qtiles, g.n_chunks);
     kern<<<grid, kGThreads, g.smem, st>>>(p->gc, p->d_sub, sc->x, sc->z, sc->rc, sc->n, g.chunk_len,
-                                          T, g.SB, cw, lam, gpart, g.n_qtiles, bpart);
+                                          T, g.SB, cw, lam, gpart, g.n_qtiles, bpart, p->d_dtab);
     count_launches(1);
     return check_cuda(cudaGetLastError(), "k_grad launch");
 }

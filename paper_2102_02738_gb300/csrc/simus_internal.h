@@ -193,6 +193,7 @@ struct GradGeom {
     bool ok;             // T * N <= 2048 and the shared-memory tiles fit
     int n_qtiles, n_chunks;
     int SB;              // scatterers per group (16, or 8 where shared memory is short)
+    bool tab;            // delta from the plan's table (staged in shared memory)
     int64_t chunk_len;
     size_t smem;
 };
