@@ -166,7 +166,7 @@ def allreduce_max(v, ws):
 
 
 # --------------------------------------------------------------------- CPU oracle
-def oracle_sample(w, target_s=12.0, max_bins=None):
+def oracle_sample(w, target_s=12.0, max_bins=None, bins=None):
     """Time the oracle's RF spectrum on a subset of kept bins (all scatterers, all
     transmits); returns (terms/s, seconds, bins used, threads, bin list, spectrum)."""
     from oracle import oracle
@@ -175,12 +175,12 @@ def oracle_sample(w, target_s=12.0, max_bins=None):
     per_bin = w.n_scat * nu * w.cfg["n_elements"] * w.n_tx
     cores = len(os.sched_getaffinity(0))
     # calibrate on as many bins as there are cores (one bin per thread)
-    k = max(1, min(nb, cores))
+    k = max(1, min(nb, cores if bins is None else bins))
     qs = np.linspace(lo, hi, k).round().astype(int)
     t0 = time.perf_counter()
     X = oracle.rf_spectrum(w.cfg, w.delays, w.apod, w.x, w.y, w.z, w.rc, qs)
     dt = time.perf_counter() - t0
-    if dt < target_s:
+    if dt < target_s and bins is None:
         k2 = int(min(nb, max(k, k * target_s / max(dt, 1e-3))))
         k2 = (k2 // cores) * cores or k2
         if max_bins:
@@ -314,7 +314,7 @@ def dtype_of(path):
 
 
 def measure_rf(ctx, name, w, path, steps, warmup, *, cpu_seconds=None, e2e=True,
-               tuning=None, oracle_ref=None):
+               tuning=None, oracle_ref=None, oracle_bins=None):
     """One simus_rf per step over the whole workload.  Returns the JSON line and the
     device tensors, plan and oracle sample for follow-up measurements."""
     torch, simus = ctx.torch, ctx.simus
@@ -397,7 +397,7 @@ def measure_rf(ctx, name, w, path, steps, warmup, *, cpu_seconds=None, e2e=True,
                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
     ref = oracle_ref
     if ref is None and cpu_seconds is not None and ctx.ws == 1:
-        v, dt, k, cores, qs, Xo = oracle_sample(w, target_s=cpu_seconds)
+        v, dt, k, cores, qs, Xo = oracle_sample(w, target_s=cpu_seconds, bins=oracle_bins)
         ref = (qs, Xo)
         line["cpu_baseline"] = {
             "value": v, "unit": "terms/s", "cores": cores, "kind": "oracle",
@@ -599,7 +599,7 @@ def measure_grad(ctx, steps, warmup, path="plain", n_scat=0, accuracy=True):
     return line
 
 
-def measure_pfield(ctx, steps, warmup, accuracy=True):
+def measure_pfield(ctx, steps, warmup, accuracy=True, n_check=60):
     """RMS field (Eq. 41-42) of the Fig. 10 L11-5v setup on a 201 x 201 x-z grid, FP32."""
     torch, simus = ctx.torch, ctx.simus
     w = ph.pfield_l11_5v()
@@ -656,7 +656,7 @@ def measure_pfield(ctx, steps, warmup, accuracy=True):
             "gpu_launches": launches, "clocks": clk}
     if accuracy and ctx.ws == 1:
         from oracle import oracle as orc
-        sel = np.linspace(0, npts - 1, 60).astype(np.int64)
+        sel = np.linspace(0, npts - 1, n_check).astype(np.int64)
         t0 = time.time()
         ref = orc.pfield(cfg, w.delays, w.apod, w.x[sel], None, w.z[sel], nf)
         dt = time.time() - t0
@@ -699,6 +699,19 @@ def other_configs(ctx, headline_ref):
     out["planewave-linear-128"] = compact(line)
     out["planewave-linear-128-grad"] = compact(measure_grad(ctx, 5, 2))
     out["ragged-batch-x0.05"] = compact(measure_batch(ctx, 256, 0.05, "tc_f16", 2, 1))
+    # the paper's other models on the same kernels: RMS field (Eq. 41-42), the 2-D model
+    # (Section V) and scatterers off the azimuth plane (Eq. 14 with Y != 0)
+    out["pfield-l11-5v"] = compact(measure_pfield(ctx, 5, 2, n_check=20))
+    w = ph.planewave_linear_128_2d()
+    line, st = measure_rf(ctx, "planewave-linear-128-2d", w, "plain", 5, 2, cpu_seconds=0.0, e2e=False)
+    st["plan"].close()
+    out["planewave-linear-128-2d"] = compact(line)
+    w = ph.diverging_convex_128_3d()
+    # (no oracle sample here: with Y != 0 one bin takes the oracle ~14 s; the parity tests
+    # cover this path)
+    line, st = measure_rf(ctx, "diverging-convex-128-3d", w, "tc_f16", 3, 1, e2e=False)
+    st["plan"].close()
+    out["diverging-convex-128-3d"] = compact(line)
     w = WORKLOADS[DEFAULT_WORKLOAD]()
     line, st = measure_rf(ctx, DEFAULT_WORKLOAD, w, "tc_bf16", 5, 2, e2e=False,
                           oracle_ref=headline_ref)

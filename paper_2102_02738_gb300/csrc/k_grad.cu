@@ -388,27 +388,40 @@ __global__ void k_grad_reduce_scat(const float *__restrict__ gpart, int n_qtiles
     }
 }
 
-// g_delays[t][e] = Re sum_k i w_k c_te(k) sum_chunk B[chunk][t][k][e].
-__global__ void k_grad_delays(const float2 *__restrict__ bpart, int n_chunks, int T, int N, int nq,
-                              int q_lo, double df, const float2 *__restrict__ cw,
-                              float *__restrict__ gd) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= T * N) return;
-    const int t = i / N, e = i - t * N;
+// g_delays[t][e] = Re sum_k i w_k c_te(k) sum_chunk B[chunk][t][k][e].  A block takes 32
+// consecutive channels (t, e) x 16 slices of the bins (k = slice, slice + 16, ...): the
+// threads of a warp read 32 consecutive elements of one (chunk, t, k) row, and the slices'
+// FP64 partial sums are added in a fixed order (reproducible).
+constexpr int kGdCh = 32, kGdSl = 16;
+__global__ void __launch_bounds__(kGdCh * kGdSl)
+k_grad_delays(const float2 *__restrict__ bpart, int n_chunks, int T, int N, int nq, int q_lo,
+              double df, const float2 *__restrict__ cw, float *__restrict__ gd) {
+    __shared__ double part[kGdSl][kGdCh];
+    const int l = threadIdx.x % kGdCh, sl = threadIdx.x / kGdCh;
+    const int i = blockIdx.x * kGdCh + l;
     double acc = 0.0;
-    for (int k = 0; k < nq; ++k) {
-        float br = 0.f, bi = 0.f;
-        for (int c = 0; c < n_chunks; ++c) {
-            const float2 b = bpart[(((size_t)c * T + t) * nq + k) * N + e];
-            br += b.x;
-            bi += b.y;
+    if (i < T * N) {
+        const int t = i / N, e = i - t * N;
+        for (int k = sl; k < nq; k += kGdSl) {
+            float br = 0.f, bi = 0.f;
+            for (int c = 0; c < n_chunks; ++c) {
+                const float2 b = bpart[(((size_t)c * T + t) * nq + k) * N + e];
+                br += b.x;
+                bi += b.y;
+            }
+            const float2 cc = cw[((size_t)t * nq + k) * N + e];
+            const double w = 6.283185307179586 * (double)(q_lo + k) * df;
+            // Re(i w c B) = -w Im(c B)
+            acc += -w * (double)(cc.x * bi + cc.y * br);
         }
-        const float2 cc = cw[((size_t)t * nq + k) * N + e];
-        const double w = 6.283185307179586 * (double)(q_lo + k) * df;
-        // Re(i w c B) = -w Im(c B)
-        acc += -w * (double)(cc.x * bi + cc.y * br);
     }
-    gd[i] = (float)acc;
+    part[sl][l] = acc;
+    __syncthreads();
+    if (sl == 0 && i < T * N) {
+        double a = 0.0;
+        for (int j = 0; j < kGdSl; ++j) a += part[j][l];
+        gd[i] = (float)a;
+    }
 }
 
 GradGeom grad_geometry(const simus_plan *p, int T, int64_t S) {
@@ -476,8 +489,8 @@ int launch_grad_finish(const simus_plan *p, const GradGeom &g, int T, int64_t S,
     }
     if (g_delays) {
         const int n = T * p->N;
-        k_grad_delays<<<(n + 127) / 128, 128, 0, st>>>(bpart, g.n_chunks, T, p->N, p->nq, p->q_lo,
-                                                      p->gc.df, cw, g_delays);
+        k_grad_delays<<<(n + kGdCh - 1) / kGdCh, kGdCh * kGdSl, 0, st>>>(bpart, g.n_chunks, T, p->N, p->nq,
+                                                                       p->q_lo, p->gc.df, cw, g_delays);
         count_launches(1);
         return check_cuda(cudaGetLastError(), "k_grad_delays launch");
     }
