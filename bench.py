@@ -427,10 +427,21 @@ def measure_plain_compare(ctx, w, st, steps):
 
     ms, stages, _, clk = ctx.timed(step, steps, 1, plans=[pplan])
     med = statistics.median(ms)
+    info = pplan.info
     pplan.close()
+    kern = statistics.median(s["green_contract"] for s in stages[0])
+    # the plain kernel's own budget per (bin, scatterer): M Green's terms at 85 FP32-pipe
+    # instructions and the two complex contractions over (element, transmit) of Eq. 29 and
+    # Eq. 32 at 4 FMA each, on the 128 FP32 lanes of an SM
+    M, N, T = info["n_sub"] * info["n_elements"], info["n_elements"], w.n_tx
+    pairs = float(info["n_bins"]) * w.n_scat
+    peak = ctx.n_sm * ctx.mhz * 1e6 * 128.0 / (FP32_PER_TERM * M + 8.0 * N * T)
     return {"value": st["terms"] / (med / 1e3), "unit": "terms/s", "steps": steps,
             "ms_per_step_median": med, "ms_per_step_min": min(ms), "ms_per_step_max": max(ms),
-            "kernel_ms_median": statistics.median(s["green_contract"] for s in stages[0]),
+            "kernel_ms_median": kern,
+            "roofline": {"bound": "alu", "achieved": pairs / (kern / 1e3) / 1e9, "peak": peak / 1e9,
+                         "unit": "G(bin x scatterer)/s", "frac": pairs / (kern / 1e3) / peak,
+                         "peak_source": f"SMs*clk*128 / (85 M + 8 N T), M={M}, N={N}, T={T}"},
             "clocks": clk}
 
 

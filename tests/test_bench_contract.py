@@ -48,3 +48,11 @@ def test_reference_arm_line():
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["e2e"]["value"] == d["value"]
+    # the same config dict as the GPU arm prints for this workload
+    import bench
+    from oracle import oracle
+    from paper_2102_02738_gb300 import phantoms as ph
+    w = ph.focused_linear_64()
+    lo, hi, nb = oracle.bins(w.cfg)
+    assert d["config"] == json.loads(json.dumps(bench.workload_config("focused-linear-64", w, nb,
+                                                                      oracle.nsub(w.cfg))))
