@@ -425,7 +425,7 @@ def measure_plain_compare(ctx, w, st, steps):
         pplan.rf(d["delays"], d["apod"], d["x"], d.get("y"), d["z"], d["rc"], out=rf,
                  stream=ctx.stream)
 
-    ms, stages, _, clk = ctx.timed(step, steps, 1, plans=[pplan])
+    ms, stages, _, clk = ctx.timed(step, steps, 3, plans=[pplan])
     med = statistics.median(ms)
     info = pplan.info
     pplan.close()
@@ -709,7 +709,7 @@ def other_configs(ctx, headline_ref):
     st["plan"].close()
     out["planewave-linear-128"] = compact(line)
     out["planewave-linear-128-grad"] = compact(measure_grad(ctx, 5, 2))
-    out["ragged-batch-x0.05"] = compact(measure_batch(ctx, 256, 0.05, "tc_f16", 2, 1))
+    out["ragged-batch-x0.05"] = compact(measure_batch(ctx, 256, 0.05, "tc_f16", 2, 3))
     # the paper's other models on the same kernels: RMS field (Eq. 41-42), the 2-D model
     # (Section V) and scatterers off the azimuth plane (Eq. 14 with Y != 0)
     out["pfield-l11-5v"] = compact(measure_pfield(ctx, 5, 2, n_check=20))
@@ -720,7 +720,7 @@ def other_configs(ctx, headline_ref):
     w = ph.diverging_convex_128_3d()
     # (no oracle sample here: with Y != 0 one bin takes the oracle ~14 s; the parity tests
     # cover this path)
-    line, st = measure_rf(ctx, "diverging-convex-128-3d", w, "tc_f16", 3, 1, e2e=False)
+    line, st = measure_rf(ctx, "diverging-convex-128-3d", w, "tc_f16", 3, 3, e2e=False)
     st["plan"].close()
     out["diverging-convex-128-3d"] = compact(line)
     w = WORKLOADS[DEFAULT_WORKLOAD]()

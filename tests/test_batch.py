@@ -104,6 +104,30 @@ def test_ragged_batch_plain_matches_oracle(S, oracle):
         assert rel_l2(rf.cpu().numpy(), oracle_rf(oracle, w)) <= TOL_F32, w.name
 
 
+@pytest.mark.parametrize("path,tol", [("plain", TOL_F32), ("tc_f16", TOL_TC)])
+def test_batch_spectrum_matches_single_calls_and_oracle(S, oracle, path, tol):
+    """simus_batch_rf_spectrum returns each simulation's spectrum before the inverse DFT:
+    the same as simus_rf_spectrum on its own plan (up to the work split's summation order)
+    and the oracle's at every kept bin."""
+    sims = ragged(n_sims=3, seed=1007)
+    plans = [S.Plan(w.cfg, path=path) for w in sims]
+    txs = [(dev(w.delays), dev(w.apod)) for w in sims]
+    scs = [(dev(w.x), None, dev(w.z), dev(w.rc)) for w in sims]
+    specs = [torch.empty((w.n_tx, w.cfg["n_elements"], p.n_bins, 2), device="cuda")
+             for w, p in zip(sims, plans)]
+    S.simus_batch_rf_spectrum([p.handle for p in plans], txs, scs, specs)
+    S.simus_plan_check(plans[0].handle)
+    for w, p, sp, tx, sc in zip(sims, plans, specs, txs, scs):
+        got = torch.view_as_complex(sp).cpu().numpy()
+        one = p.rf_spectrum(*tx, *sc).cpu().numpy()
+        qs = np.arange(p.info["q_lo"], p.info["q_hi"] + 1)
+        ref = oracle.rf_spectrum(w.cfg, w.delays, w.apod, w.x, w.y, w.z, w.rc, qs)
+        assert rel_l2(got, one) <= tol, w.name
+        assert rel_l2(got, ref) <= tol, w.name
+    for p in plans:
+        p.close()
+
+
 def test_batch_with_an_empty_simulation(S):
     sims = ragged(n_sims=3)
     sims[1].x, sims[1].z, sims[1].rc = (np.zeros(0, np.float32),) * 3
