@@ -53,7 +53,10 @@ extern "C" {
  *               rounded to FP16, and both contractions (transmit sum Eq. 29 and
  *               receive sum Eq. 32) run on the tcgen05 tensor cores with FP32
  *               accumulation in tensor memory.
- *   TC_BF16   : as TC_F16 with BF16 operands. */
+ *   TC_BF16   : as TC_F16 with BF16 operands, each FP32 value carried as a BF16 leading
+ *               part and a BF16 remainder and each GEMM formed as three products
+ *               (hi hi' + hi rem' + rem hi'), which keeps ~16 significant bits; arrays of
+ *               up to 176 elements (wider ones return SIMUS_ERR_UNSUPPORTED). */
 #define SIMUS_PATH_PLAIN_F32 0
 #define SIMUS_PATH_TC_F16 1
 #define SIMUS_PATH_TC_BF16 2

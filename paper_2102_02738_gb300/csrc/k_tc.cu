@@ -125,7 +125,7 @@ TcShape tc_shape(const simus_plan *p, int T, int64_t S, double work_share, int i
                 const int nN = ((2 * TG + 15) / 16) * 16;
                 const int G = (T + TG - 1) / TG;
                 if (per > 1 && G > 2) break;
-                if (nN + stash > 512) continue;
+                if (nN > 256 || nN + stash > 512) continue;   // (an M = 128 MMA takes N <= 256)
                 const int qb = (512 - nN - stash) / (nN * G * g.mh);
                 if (qb < per) continue;
                 const size_t sm = unit_smem(g.Np, nN, nbuf, p->M, tab_n, split);
