@@ -2,8 +2,9 @@
 // work items of any number of simulations.
 //
 // The Green's tile G_e(q, s, e) of a bin q and a tile of 128 scatterers is generated once
-// in FP32 (Eq. 17/20/39/40, sub-element sum of Eq. 33), rounded to FP16 (or BF16) in
-// shared memory, and feeds two complex contractions written as real GEMMs:
+// in FP32 (Eq. 17/20/39/40, sub-element sum of Eq. 33), rounded to FP16 (or split into BF16
+// leading parts and remainders, three products per GEMM) in shared memory, and feeds two
+// complex contractions written as real GEMMs:
 //
 //   transmit sum (Eq. 29)   P[s][t]  = sum_e G[s][e] C_q[t][e]
 //       A  = [Re G | Im G]                      128 x 2Np   (rows s, K over e), K-major
