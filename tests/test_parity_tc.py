@@ -104,6 +104,20 @@ def test_tc_bf16_meets_the_reduced_precision_budget(S, oracle):
     assert err <= TOL_TC
 
 
+@pytest.mark.parametrize("pair", [0, 1])
+def test_tc_bf16_pass_modes(S, oracle, pair):
+    """Split BF16 with one-bin (pair 0) and two-bin (pair 1, one stash slot of 2 Np
+    columns) generation passes, set through the tuning interface."""
+    w = ph.tiny(convex=True, n_elements=24, n_scat=400, n_tx=9)
+    ref = oracle.rf(w.cfg, w.delays, w.apod, w.x, w.y, w.z, w.rc)
+    plan = S.Plan(w.cfg, path="tc_bf16")
+    plan.set_tuning(pair=pair, max_bins=4)
+    got = plan.rf(*[dev(a) for a in (w.delays, w.apod, w.x, w.y, w.z, w.rc)]).cpu().numpy()
+    assert S.lib.simus_plan_check(plan.handle) == 0
+    plan.close()
+    assert rel_l2(got, ref) <= TOL_TC
+
+
 def test_tc_bf16_rejects_arrays_wider_than_the_split_tile(S):
     """The leading-part and remainder tiles of more than 176 elements do not fit one
     CTA's shared memory: SIMUS_ERR_UNSUPPORTED before any launch; FP16 takes them."""
