@@ -241,19 +241,22 @@ int simus_plan_get_timings(simus_plan *plan, float *ms);
  *                 (two shared-memory tile buffers and a tensor-memory stash; default),
  *                 1 two (two buffers), 0 one; the largest that fits at most this
  *   delta_table   1: delta from the table where Y = 0 (default), 0: direct evaluation
+ *   tile_buffers  shared-memory buffers for the Green's tiles of a pass, at most: 2 (the
+ *                 default) or 1 (later bins of a pass wait in the tensor-memory stash)
  *   chunks        single simulations: scatterer chunks per bin tile (default: chosen by a
  *                 makespan model over the SMs)
  * The project's autotuner (paper_2102_02738_gb300/autotune.py) times candidates through
  * these calls and caches the fastest per problem shape.
  * Returns SIMUS_ERR_ARG for a NULL plan or values out of range (max_bins > 64,
- * items_per_sm > 1024, chunks > 65536, pair > 2, delta_table > 1). */
+ * items_per_sm > 1024, chunks > 65536, pair > 2, delta_table > 1, tile_buffers > 2). */
 typedef struct simus_tuning {
     int32_t items_per_sm;
     int32_t max_bins;
     int32_t pair;
     int32_t delta_table;
     int32_t chunks;
-    int32_t reserved[3];
+    int32_t tile_buffers;
+    int32_t reserved[2];
 } simus_tuning;
 int simus_plan_set_tuning(simus_plan *plan, const simus_tuning *tuning);
 int simus_plan_get_tuning(const simus_plan *plan, simus_tuning *tuning);

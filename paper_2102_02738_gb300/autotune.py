@@ -2,8 +2,8 @@
 
 For a problem shape -- device, contraction path, elements N, sub-elements nu, transmits T,
 kept bins, scatterer count S rounded to a power of two -- it times candidate tunings
-(`simus_tuning`: bins per work item, one or two tile buffers, delta table, scatterer
-chunks; items per SM for batches) through the library's own entry points with CUDA
+(`simus_tuning`: bins per work item, bins per generation pass, one or two tile buffers,
+delta table, scatterer chunks; items per SM for batches) through the library's own entry points with CUDA
 events, keeps the fastest and caches it in a JSON file, so later plans of the same
 shape start from it without timing.  Results do not depend on the tuning beyond FP32
 summation order (and the delta table's 2.3e-6 relative error), so tuning never changes
@@ -35,16 +35,18 @@ def shape_key(plan: simus.Plan, T: int, S: int, batch: int = 1) -> str:
 
 
 def candidates(single: bool = True):
-    """Tunings to time: bins per item x tile buffers x delta table (x items per SM for
-    batches).  Chunk counts are left to the library's makespan model, plus two fixed
-    alternatives around it for single simulations."""
+    """Tunings to time: bins per item x bins per generation pass x tile buffers (passes of
+    two or three bins) x delta table (x items per SM for batches).  Chunk counts are left
+    to the library's makespan model."""
     out = []
     for mb, pair, tab in itertools.product((2, 3, 4, 6), (2, 1, 0), (1, 0)):
-        if single:
-            out.append(dict(max_bins=mb, pair=pair, delta_table=tab, chunks=0))
-        else:
-            for ips in (2, 4, 8):
-                out.append(dict(max_bins=mb, pair=pair, delta_table=tab, items_per_sm=ips))
+        for tbuf in ((2, 1) if pair > 0 else (1,)):
+            base = dict(max_bins=mb, pair=pair, delta_table=tab, tile_buffers=tbuf)
+            if single:
+                out.append(dict(base, chunks=0))
+            else:
+                for ips in (2, 4, 8):
+                    out.append(dict(base, items_per_sm=ips))
     return out
 
 

@@ -104,39 +104,46 @@ TcShape tc_shape(const simus_plan *p, int T, int64_t S, double work_share, int i
     // pass (the packed leading parts and remainders of three bins exceed the registers)
     const bool split = p->path == SIMUS_PATH_TC_BF16;
     const int ops = split ? 2 : 1;
-    // Bins per generation pass (sharing one geometry setup) and shared-memory tile
-    // buffers, most sharing first: (3, 2), (3, 1), (2, 2), (2, 1), (1, 1); bins past the
-    // buffers wait in tensor-memory stash slots of Np columns.  At most two transmit
-    // groups when bins share a pass; the delta table where it still fits; tensor memory
-    // holds D1, QB * G * mh accumulator slices of nN columns and the stash.
-    static const int kModes[5][2] = {{3, 2}, {3, 1}, {2, 2}, {2, 1}, {1, 1}};
-    for (int mi = 0; mi < 5 && !g.ok; ++mi) {
-        const int per = kModes[mi][0], nbuf = kModes[mi][1];
-        if (per > p->pair_mode + 1) continue;
-        if (split && (nbuf != 1 || per > 2)) continue;
-        const int stash = (per - nbuf) * g.Np * ops;   // tensor-memory columns of the stash
-        for (int tb = 0; tb < 2 && !g.ok; ++tb) {
-            const int tab_n = tb ? 0 : tab_full;
-            if (tb && !tab_full) break;
-            // transmit-group sizes, largest first: FP16 steps down by 8; split BF16 (whose
-            // operands fill shared memory at smaller groups) takes the largest size of
-            // each group count, ceil(T / G)
-            for (int TG = std::min(T, 120), G0 = 1; TG >= 1 && !g.ok;
-                 TG = split ? (G0 < T ? (T + G0) / (G0 + 1) : 0) : (TG > 8 ? TG - 8 : TG - 1), ++G0) {
-                const int nN = ((2 * TG + 15) / 16) * 16;
-                const int G = (T + TG - 1) / TG;
-                if (per > 1 && G > 2) break;
-                if (nN > 256 || nN + stash > 512) continue;   // (an M = 128 MMA takes N <= 256)
-                const int qb = (512 - nN - stash) / (nN * G * g.mh);
-                if (qb < per) continue;
-                const size_t sm = unit_smem(g.Np, nN, nbuf, p->M, tab_n, split);
-                if (sm > limit) continue;
-                g.ok = true;
-                g.TG = TG; g.nN = nN; g.pair = per - 1; g.nbuf = nbuf; g.n_groups = G;
-                g.tab_n = tab_n;
-                g.QB = std::min(std::max(p->max_bins, per), qb);
-                g.QB -= g.QB % per;
-                g.smem = sm + kHeader;
+    // Preference, measured on the ragged batch: the delta table first (without it the
+    // generation costs about 1.5 times as much); then more bins per generation pass
+    // (3, 2, 1: sharing one geometry setup); then fewer transmit groups (each group
+    // repeats MMA1, P' and MMA2 over the whole tile: one group with one tile buffer beat
+    // two groups with two buffers by 11-16 %); then two shared-memory tile buffers over
+    // one.  Bins past the buffers wait in tensor-memory stash slots of Np columns; at most
+    // two transmit groups when bins share a pass; tensor memory holds D1, QB * G * mh
+    // accumulator slices of nN columns and the stash.
+    for (int tb = 0; tb < 2 && !g.ok; ++tb) {
+        const int tab_n = tb ? 0 : tab_full;
+        if (tb && !tab_full) break;
+        for (int per = 3; per >= 1 && !g.ok; --per) {
+            if (per > p->pair_mode + 1) continue;
+            if (split && per > 2) continue;
+            for (int nbuf = std::min(per, 2); nbuf >= 1; --nbuf) {
+                if (split && nbuf != 1) continue;
+                if (nbuf > p->tile_buffers) continue;
+                const int stash = (per - nbuf) * g.Np * ops;   // tensor-memory columns of the stash
+                // transmit-group sizes, largest first: FP16 steps down by 8; split BF16
+                // (whose operands fill shared memory at smaller groups) takes the largest
+                // size of each group count, ceil(T / G)
+                for (int TG = std::min(T, 120), G0 = 1; TG >= 1;
+                     TG = split ? (G0 < T ? (T + G0) / (G0 + 1) : 0) : (TG > 8 ? TG - 8 : TG - 1), ++G0) {
+                    const int nN = ((2 * TG + 15) / 16) * 16;
+                    const int G = (T + TG - 1) / TG;
+                    if (per > 1 && G > 2) break;
+                    if (g.ok && G >= g.n_groups) break;           // not fewer groups than found
+                    if (nN > 256 || nN + stash > 512) continue;   // (an M = 128 MMA takes N <= 256)
+                    const int qb = (512 - nN - stash) / (nN * G * g.mh);
+                    if (qb < per) continue;
+                    const size_t sm = unit_smem(g.Np, nN, nbuf, p->M, tab_n, split);
+                    if (sm > limit) continue;
+                    g.ok = true;
+                    g.TG = TG; g.nN = nN; g.pair = per - 1; g.nbuf = nbuf; g.n_groups = G;
+                    g.tab_n = tab_n;
+                    g.QB = std::min(std::max(p->max_bins, per), qb);
+                    g.QB -= g.QB % per;
+                    g.smem = sm + kHeader;
+                    break;
+                }
             }
         }
     }

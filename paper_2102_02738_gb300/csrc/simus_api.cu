@@ -488,13 +488,14 @@ int simus_plan_set_profiling(simus_plan *plan, int32_t enable) {
 int simus_plan_set_tuning(simus_plan *plan, const simus_tuning *t) {
     if (!plan || !t) return fail(SIMUS_ERR_ARG, "plan and tuning must not be NULL");
     if (t->items_per_sm > 1024 || t->max_bins > 64 || t->chunks > 65536 || t->pair > 2 ||
-        t->delta_table > 1)
+        t->delta_table > 1 || t->tile_buffers > 2)
         return fail(SIMUS_ERR_ARG, "tuning value out of range");
     plan->items_per_sm = t->items_per_sm > 0 ? t->items_per_sm : 4;
     plan->max_bins = t->max_bins > 0 ? t->max_bins : 4;
     plan->pair_mode = t->pair >= 0 ? t->pair : 2;
     plan->delta_table = t->delta_table >= 0 ? t->delta_table : 1;
     plan->chunks = t->chunks > 0 ? t->chunks : 0;
+    plan->tile_buffers = t->tile_buffers > 0 ? t->tile_buffers : 2;
     return SIMUS_OK;
 }
 
@@ -506,6 +507,7 @@ int simus_plan_get_tuning(const simus_plan *plan, simus_tuning *t) {
     t->pair = plan->pair_mode;
     t->delta_table = plan->delta_table;
     t->chunks = plan->chunks;
+    t->tile_buffers = plan->tile_buffers;
     return SIMUS_OK;
 }
 

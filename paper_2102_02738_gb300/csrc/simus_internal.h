@@ -69,6 +69,7 @@ struct simus_plan {
     int max_bins = 4;
     int pair_mode = 2;
     int delta_table = 1;
+    int tile_buffers = 2;
     int chunks = 0;
     bool profiling = false;
     bool stage_used[SIMUS_N_STAGES] = {};

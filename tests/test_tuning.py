@@ -19,8 +19,9 @@ TOL_TC = 2e-3
 def test_candidates_cover_the_knobs():
     from paper_2102_02738_gb300 import autotune
     c = autotune.candidates(single=True)
-    assert {k for d in c for k in d} == {"max_bins", "pair", "delta_table", "chunks"}
+    assert {k for d in c for k in d} == {"max_bins", "pair", "delta_table", "chunks", "tile_buffers"}
     assert {d["pair"] for d in c} == {0, 1, 2} and {d["delta_table"] for d in c} == {0, 1}
+    assert {d["tile_buffers"] for d in c if d["pair"] > 0} == {1, 2}
     cb = autotune.candidates(single=False)
     assert {d["items_per_sm"] for d in cb} == {2, 4, 8}
     assert {d["max_bins"] for d in c} == {2, 3, 4, 6}
@@ -49,15 +50,19 @@ def rel_l2(a, b):
 def test_set_get_round_trip(S):
     w = ph.tiny(n_elements=16, n_scat=50, n_tx=3)
     plan = S.Plan(w.cfg, path="tc_f16")
-    assert plan.get_tuning() == dict(items_per_sm=4, max_bins=4, pair=2, delta_table=1, chunks=0)
-    plan.set_tuning(max_bins=6, pair=0, delta_table=0, chunks=3, items_per_sm=8)
-    assert plan.get_tuning() == dict(items_per_sm=8, max_bins=6, pair=0, delta_table=0, chunks=3)
-    plan.set_tuning(max_bins=-1, pair=-1, delta_table=-1, chunks=0, items_per_sm=-1)
-    assert plan.get_tuning() == dict(items_per_sm=4, max_bins=4, pair=2, delta_table=1, chunks=0)
+    default = dict(items_per_sm=4, max_bins=4, pair=2, delta_table=1, chunks=0, tile_buffers=2)
+    assert plan.get_tuning() == default
+    plan.set_tuning(max_bins=6, pair=0, delta_table=0, chunks=3, items_per_sm=8, tile_buffers=1)
+    assert plan.get_tuning() == dict(items_per_sm=8, max_bins=6, pair=0, delta_table=0, chunks=3,
+                                     tile_buffers=1)
+    plan.set_tuning(max_bins=-1, pair=-1, delta_table=-1, chunks=0, items_per_sm=-1, tile_buffers=0)
+    assert plan.get_tuning() == default
     with pytest.raises(S.SimusError):
         plan.set_tuning(max_bins=65)
     with pytest.raises(S.SimusError):
         plan.set_tuning(pair=3)
+    with pytest.raises(S.SimusError):
+        plan.set_tuning(tile_buffers=3)
     plan.close()
 
 
@@ -67,7 +72,9 @@ def test_set_get_round_trip(S):
                                  dict(max_bins=3, pair=2, delta_table=0, chunks=3),
                                  dict(max_bins=6, pair=1, delta_table=0, chunks=2),
                                  dict(max_bins=3, pair=0, delta_table=1, chunks=1),
-                                 dict(max_bins=8, pair=0, delta_table=0)])
+                                 dict(max_bins=8, pair=0, delta_table=0),
+                                 dict(max_bins=6, pair=2, delta_table=1, tile_buffers=1),
+                                 dict(max_bins=4, pair=1, delta_table=0, tile_buffers=1)])
 def test_every_tuning_matches_the_oracle(S, oracle, tun):
     w = ph.tiny(convex=True, n_elements=24, n_scat=400, n_tx=9)
     ref = oracle.rf(w.cfg, w.delays, w.apod, w.x, w.y, w.z, w.rc)
