@@ -3,14 +3,18 @@
 // With drf = dL/drf and Lambda_q(e,t) = H_q sum_j drf[t][e][j] e^{-2 pi i q j / Nt} (the
 // adjoint of the inverse DFT and of the transfer factor), dL = Re sum Lambda dRF_q.  Per
 // bin q and scatterer s, with c_te = W e^{i w dtau} and G_e = sum_mu g (Eq. 33):
-//   P_t = sum_e c_te G_e,   A_t = sum_e Lambda_te G_e      (and the same with dG/dX, dG/dZ)
+//   P_t = sum_e c_te G_e,   A_t = sum_e Lambda_te G_e
 //   dL/dR_s      += Re sum_t A_t P_t
-//   dL/dX_s      += R_s Re sum_t (A_t Px_t + P_t Ax_t),   dL/dZ_s likewise
+//   dL/dX_s      += R_s Re sum_t (A_t Px_t + P_t Ax_t)   (Px, Ax: the same sums of dG/dX)
+//                 = R_s Re sum_e dG_e/dX W_e,   W_e = sum_t (A_t c_te + P_t Lambda_te),
+//   dL/dZ_s likewise with dG/dZ,
 //   B_q(t,e)     += R_s A_t G_e,   dL/d dtau_te = Re sum_q i w_q c_te B_q(t,e).
-// Green's terms and their derivatives are recomputed here, never stored across calls.
+// The second form of dL/dX needs two contractions of the Green's tile (P, A) and one of
+// the transmit weights (W) instead of six of the three tiles.  Green's terms and their
+// derivatives are recomputed here, never stored across calls.
 //
 // Kernels: k_adjoint_dft (Lambda), k_grad (per tile of QB bins x chunk of scatterers,
-// groups of SB scatterers: generation -> contraction -> B accumulation; per-bin-tile
+// groups of SB scatterers: generation -> P, A -> W and B accumulation; per-bin-tile
 // partial gradients and per-chunk partial B, reduced in a fixed order afterwards),
 // k_grad_reduce_scat, k_grad_delays.
 #include <algorithm>
@@ -22,23 +26,45 @@ namespace simus {
 
 namespace {
 constexpr int kGThreads = 384;  // 12 warps: the register budget of the generation allows it
+constexpr int kGWarps = kGThreads / 32;
 constexpr int kGQB = 2;     // bins per tile
 constexpr int kGSBMax = 16; // scatterers per group (16, or 8 where shared memory is short)
-constexpr int kGRT = 2;     // transmits per thread in the contraction (register block)
 
-// Threads sharing one (bin, scatterer, transmit pair) item of the contraction along the
-// elements (1, 2, 4 or 8): as many as keep two items per thread or fewer.
+// P, A products: an item is (bin, 4 scatterers, 2 transmits) with both weight sets (32
+// accumulators); ks threads (1, 2, 4 or 8) share an item along the elements, as many as
+// keep every item's threads within 384.
 __host__ __device__ inline int grad_ks(int SB, int T) {
-    const int items = kGQB * SB * ((T + kGRT - 1) / kGRT);
+    const int items = kGQB * (SB / 4) * ((T + 1) / 2);
     int ks = 1;
     while (ks < 8 && items * ks * 2 <= kGThreads) ks *= 2;
     return ks;
 }
-// Row stride (complex values) of the G, dG/dX, dG/dZ tiles: N rounded up to ks mod 16, so
-// that the rows of consecutive scatterers start 2 ks words apart and the ks lanes of an item
-// (elements e, e + 1, ...) and the items of the next scatterer fall in distinct banks.
-__host__ __device__ inline int grad_row(int N, int ks) {
-    return N + (((ks - N) % 16) + 16) % 16;
+// Row strides (complex values): Green's tiles N rounded up to 2 mod 4 (the rows of
+// scatterers four apart, read by one P, A load, start in different bank halves); weight
+// and adjoint-spectrum rows N rounded up to 4 mod 8 (the rows of transmits two apart,
+// read by one P, A load, start 16 words apart).
+__host__ __device__ inline int grad_row(int N) { return N + (((2 - N) % 4) + 4) % 4; }
+__host__ __device__ inline int grad_wrow(int N) { return N + (((4 - N) % 8) + 8) % 8; }
+
+// Halve n live values across the lanes xor o: lanes with bit o clear keep the lower half,
+// the others the upper half, each summed with its partner's copy.
+template <int NV, int O>
+__device__ __forceinline__ void halve_lanes(float (&v)[32], int lane) {
+    const bool up = (lane & O) != 0;
+#pragma unroll
+    for (int i = 0; i < NV / 2; ++i) {
+        const float send = up ? v[i] : v[i + NV / 2];
+        const float keep = up ? v[i + NV / 2] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, O);
+    }
+}
+// Sum the 32 accumulators of a P, A item over its KS lanes (consecutive lanes, part =
+// lane mod KS): afterwards part p holds the values p (32/KS) .. + 32/KS - 1 in v[0..].
+template <int KS>
+__device__ __forceinline__ void reduce_item(float (&v)[32], int lane) {
+    if (KS >= 8) halve_lanes<32, 4>(v, lane);
+    if (KS >= 4) halve_lanes<(KS >= 8 ? 16 : 32), 2>(v, lane);
+    if (KS >= 2) halve_lanes<(KS >= 8 ? 8 : (KS >= 4 ? 16 : 32)), 1>(v, lane);
 }
 }  // namespace
 
@@ -102,9 +128,10 @@ k_adjoint_dft(const float *__restrict__ drf, int N, int n_chan, int nq, int q_lo
 // [mu][e] (centroid; normal and rotated centroid), so that the threads of a warp, which
 // take consecutive elements, read consecutive 16-byte words instead of 32-byte records
 // nu apart.  TAB: delta and d delta/dr from the plan's cubic pieces (staged after the other
-// tiles; the derivative of the piece in its variable times dx/dr), and the phase and
-// absorption of the tile's second bin from the first by one phasor step; points within
-// ~2 mm of a sub-element, outside the table, take the direct four-Gaussian form.
+// tiles; the derivative of the piece in its variable times dx/dr); points within ~2 mm of
+// a sub-element, outside the table, take the direct four-Gaussian form.  The phase of
+// every bin is reduced exactly (double-float q u) and its absorption is the previous
+// bin's times exp(-k_a r df / c).
 template <bool NARROW, bool TAB>
 __global__ void __launch_bounds__(kGThreads, 1)
 k_grad(const GreenConst gc, const SubElem *__restrict__ sub_g, const float *__restrict__ xg,
@@ -113,22 +140,24 @@ k_grad(const GreenConst gc, const SubElem *__restrict__ sub_g, const float *__re
        float *__restrict__ gpart /*[3][n_qtiles][S]*/, int n_qtiles,
        float2 *__restrict__ bpart /*[n_chunks][T][nq][N]*/, const float4 *__restrict__ dtab) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int N = gc.N, nu = gc.nu, M = gc.M, nq = gc.nq, Nr = N + 1;
-    const int tid = threadIdx.x;
+    const int N = gc.N, nu = gc.nu, M = gc.M, nq = gc.nq;
+    const int Nr = grad_wrow(N), NrG = grad_row(N);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int QB = kGQB;
     const int ks = grad_ks(SB, T);
-    const int NrG = grad_row(N, ks);
+    const int NCH = (N + 63) >> 6;                                  // 64-element chunks
+    const int nit = QB * SB * T;
     float4 *sc = reinterpret_cast<float4 *>(smem_raw);              // [SB] (x, 0, z, R)
     float4 *subA = sc + kGSBMax;                                     // [nu][N] xh, xl, zh, zl
     float4 *subB = subA + M;                                        // [nu][N] cpsi, spsi, l0, z0
-    float2 *cwt = reinterpret_cast<float2 *>(subB + M);             // [QB][T][Nr]
+    float4 *AP = subB + M;                                          // [QB][SB][T] (A_t, P_t)
+    float2 *cwt = reinterpret_cast<float2 *>(AP + nit);             // [QB][T][Nr]
     float2 *lat = cwt + QB * T * Nr;                                // [QB][T][Nr]
     float2 *Bt = lat + QB * T * Nr;                                 // [QB][T][N]
     float2 *Gt = Bt + QB * T * N;                                   // [3][QB][SB][NrG]
-    float2 *RA = Gt + 3 * QB * SB * NrG;                            // [QB][SB][T]
-    float *sg = reinterpret_cast<float *>(RA + QB * SB * T);        // [3][QB*SB*T]
-    const int nit = QB * SB * T;
-    float4 *tabs = reinterpret_cast<float4 *>(sg + 3 * nit);        // [2 tab_n] (TAB)
+    float *sg = reinterpret_cast<float *>(Gt + 3 * QB * SB * NrG);  // [QB][SB][T] Re A_t P_t
+    float *xz = sg + nit;                                           // [2][QB][SB][NCH]
+    float4 *tabs = reinterpret_cast<float4 *>(xz + ((2 * QB * SB * NCH + 3) & ~3));  // (TAB)
 
     const int qt = blockIdx.x, chunk = blockIdx.y;
     const int k0 = qt * QB;
@@ -152,12 +181,13 @@ k_grad(const GreenConst gc, const SubElem *__restrict__ sub_g, const float *__re
         Bt[i] = make_float2(0.f, 0.f);
     }
     const float q0 = (float)(gc.q_lo + k0);
-    // contraction work: (bin, scatterer, pair of transmits) items, each split over ks
-    // threads along the elements when there are fewer items than threads
-    const int TB = (T + kGRT - 1) / kGRT;
-    const int items = QB * SB * TB;
-    const int units = items * ks;
     const size_t plane = (size_t)QB * SB * NrG;
+    // P, A items: (bin, 4 scatterers, 2 transmits), ks threads each
+    const int TB = (T + 1) >> 1, SB4 = SB >> 2;
+    const int units = QB * SB4 * TB * ks;
+    // W and B work, one warp per unit: W units (bin, 4 scatterers, 64 elements), then B
+    // units (bin, 4 transmits, 64 elements); two elements per lane, 32 apart
+    const int nW = QB * SB4 * NCH, nWB = nW + QB * ((T + 3) >> 2) * NCH;
 
     for (int64_t sb = s_begin; sb < s_end; sb += SB) {
         __syncthreads();
@@ -181,23 +211,19 @@ k_grad(const GreenConst gc, const SubElem *__restrict__ sub_g, const float *__re
                 const PairSetup P = pair_setup<false>(gc, se, ps.x, 0.f, ps.z, q0);
                 const PairGrad Q = pair_grad(gc, se, ps.x, ps.z, P);
                 if (TAB) {
-                    // E = exp((i k - k_a) r) / r at q0 from the exact phase reduction, then
-                    // E <- E w, w = exp(-k_a r df / c) exp(2 pi i frac(u)) (as phase_run,
-                    // without the obliquity, which the derivative keeps apart)
-                    const float amp0 = gc.h * P.inv_r * ex2_a(-q0 * gc.att2 * P.rh);
-                    float sn, cs;
-                    sincos_a(6.283185307179586f * df_frac_mul(q0, P.u), sn, cs);
-                    float Er = amp0 * cs, Ei = amp0 * sn, wr = 0.f, wi = 0.f;
-                    if (QB > 1) {
-                        sincospif(2.0f * ((P.u.h - rintf(P.u.h)) + P.u.l), &sn, &cs);
-                        wr = P.mstep * cs;
-                        wi = P.mstep * sn;
-                    }
+                    // E = exp((i k - k_a) r) / r (without the obliquity, which the
+                    // derivative keeps apart): phase reduced exactly at every bin,
+                    // absorption stepped by exp(-k_a r df / c)
+                    float amp = gc.h * P.inv_r * ex2_a(-q0 * gc.att2 * P.rh);
                     const float kt = P.kap * gc.tab_inv_dx, t0 = gc.tab_x0 * gc.tab_inv_dx;
                     const float dxdr = gc.tab_inv_dx * gc.kh * gc.h2 * Q.rr2;   // per bin
 #pragma unroll
                     for (int j = 0; j < QB; ++j) {
                         const float q = q0 + (float)j;
+                        if (j > 0) amp *= P.mstep;
+                        float sn, cs;
+                        sincos_a(6.283185307179586f * df_frac_mul(q, P.u), sn, cs);
+                        const float Er = amp * cs, Ei = amp * sn;
                         const float tt = fmaf(q, kt, -t0);
                         const float fl = floorf(fminf(fmaxf(tt, 0.0f), (float)gc.tab_n - 0.5f));
                         const int i = (int)fl;
@@ -220,11 +246,6 @@ k_grad(const GreenConst gc, const SubElem *__restrict__ sub_g, const float *__re
                         G[j].x += g.x; G[j].y += g.y;
                         GX[j].x += gx.x; GX[j].y += gx.y;
                         GZ[j].x += gz.x; GZ[j].y += gz.y;
-                        if (j + 1 < QB) {
-                            const float nr = fmaf(Er, wr, -Ei * wi);
-                            Ei = fmaf(Er, wi, Ei * wr);
-                            Er = nr;
-                        }
                     }
                 } else {
 #pragma unroll
@@ -250,114 +271,204 @@ k_grad(const GreenConst gc, const SubElem *__restrict__ sub_g, const float *__re
         }
         __syncthreads();
 
-        // 2. contractions per (bin, scatterer, transmit): P = C.G, A = L.G and the same
-        // with dG/dX, dG/dZ, as a register-blocked product (one scatterer, kGRT transmits)
-        for (int base = 0; base < units; base += kGThreads) {
+
+        // 2. P_t = sum_e c_te G_e and A_t = sum_e L_te G_e for 4 scatterers x 2 transmits
+        // per item: 8 loads and 64 FMA per element; the item's ks partial sums are halved
+        // across its lanes, so that each lane ends with whole (A_t, P_t) records
+        // (an item's ks lanes are consecutive and units is a multiple of ks, so a lane
+        // past the end belongs to a wholly idle item: it runs item 0 and stores nothing)
+        for (int base = 0; base < units && base + warp * 32 < units; base += kGThreads) {
             const int w = base + tid;
             const bool act = w < units;
             const int it = act ? w / ks : 0, part = w - (w / ks) * ks;
-            const int j = it / (SB * TB), r = it - j * SB * TB, s = r / TB, tb = r - s * TB;
-            const int t0 = tb * kGRT;
-            const float2 *g0 = Gt + ((size_t)j * SB + s) * NrG;
-            const float2 *g1 = g0 + plane, *g2 = g0 + 2 * plane;
-            const float2 *cr[kGRT], *lr[kGRT];
+            const int j = it / (SB4 * TB), r = it - j * SB4 * TB, s4 = r / TB, tb = r - s4 * TB;
+            const int s0 = 4 * s4, t0 = 2 * tb;
+            const float2 *g0 = Gt + ((size_t)j * SB + s0) * NrG;
+            const float2 *cr[2], *lr[2];
 #pragma unroll
-            for (int dt = 0; dt < kGRT; ++dt) {
+            for (int dt = 0; dt < 2; ++dt) {
                 const int t = min(t0 + dt, T - 1);          // past T: a duplicate, discarded
                 cr[dt] = cwt + ((size_t)j * T + t) * Nr;
                 lr[dt] = lat + ((size_t)j * T + t) * Nr;
             }
-            // acc[dt][type][0: C, 1: L][re, im]
-            float acc[kGRT][3][2][2];
+            // v[((si 2 + dt) 2 + w) 2 + (re, im)], w = 0: P (weights c), 1: A (spectra L)
+            float v[32];
 #pragma unroll
-            for (int dt = 0; dt < kGRT; ++dt)
-#pragma unroll
-                for (int y = 0; y < 3; ++y)
-#pragma unroll
-                    for (int c = 0; c < 2; ++c) acc[dt][y][c][0] = acc[dt][y][c][1] = 0.f;
+            for (int i = 0; i < 32; ++i) v[i] = 0.f;
 #pragma unroll 2
             for (int e = part; e < N; e += ks) {
-                const float2 a[3] = {g0[e], g1[e], g2[e]};
+                float2 g[4];
 #pragma unroll
-                for (int dt = 0; dt < kGRT; ++dt) {
+                for (int si = 0; si < 4; ++si) g[si] = g0[si * NrG + e];
+#pragma unroll
+                for (int dt = 0; dt < 2; ++dt) {
                     const float2 cc = cr[dt][e], ll = lr[dt][e];
 #pragma unroll
-                    for (int y = 0; y < 3; ++y) {
-                        acc[dt][y][0][0] = fmaf(cc.x, a[y].x, fmaf(-cc.y, a[y].y, acc[dt][y][0][0]));
-                        acc[dt][y][0][1] = fmaf(cc.x, a[y].y, fmaf(cc.y, a[y].x, acc[dt][y][0][1]));
-                        acc[dt][y][1][0] = fmaf(ll.x, a[y].x, fmaf(-ll.y, a[y].y, acc[dt][y][1][0]));
-                        acc[dt][y][1][1] = fmaf(ll.x, a[y].y, fmaf(ll.y, a[y].x, acc[dt][y][1][1]));
+                    for (int si = 0; si < 4; ++si) {
+                        float *o = v + (si * 2 + dt) * 4;
+                        o[0] = fmaf(cc.x, g[si].x, fmaf(-cc.y, g[si].y, o[0]));
+                        o[1] = fmaf(cc.x, g[si].y, fmaf(cc.y, g[si].x, o[1]));
+                        o[2] = fmaf(ll.x, g[si].x, fmaf(-ll.y, g[si].y, o[2]));
+                        o[3] = fmaf(ll.x, g[si].y, fmaf(ll.y, g[si].x, o[3]));
                     }
                 }
             }
-            for (int o = 1; o < ks; o <<= 1) {              // ks adjacent lanes share an item
-#pragma unroll
-                for (int dt = 0; dt < kGRT; ++dt)
-#pragma unroll
-                    for (int y = 0; y < 3; ++y)
-#pragma unroll
-                        for (int c = 0; c < 2; ++c) {
-                            acc[dt][y][c][0] += __shfl_xor_sync(0xffffffffu, acc[dt][y][c][0], o);
-                            acc[dt][y][c][1] += __shfl_xor_sync(0xffffffffu, acc[dt][y][c][1], o);
-                        }
+            switch (ks) {
+                case 8: reduce_item<8>(v, lane); break;
+                case 4: reduce_item<4>(v, lane); break;
+                case 2: reduce_item<2>(v, lane); break;
+                default: break;
             }
-            if (act && part == 0) {
-                const float R = sc[s].w;
+            // this lane's records: (si, dt) pairs a = part (8/ks) + m
+            const int nrec = 8 / ks;
 #pragma unroll
-                for (int dt = 0; dt < kGRT; ++dt) {
-                    const int t = t0 + dt;
-                    if (t < T) {
-                        const float Pr = acc[dt][0][0][0], Pi = acc[dt][0][0][1];
-                        const float Ar = acc[dt][0][1][0], Ai = acc[dt][0][1][1];
-                        const float Pxr = acc[dt][1][0][0], Pxi = acc[dt][1][0][1];
-                        const float Axr = acc[dt][1][1][0], Axi = acc[dt][1][1][1];
-                        const float Pzr = acc[dt][2][0][0], Pzi = acc[dt][2][0][1];
-                        const float Azr = acc[dt][2][1][0], Azi = acc[dt][2][1][1];
-                        const int o = (j * SB + s) * T + t;
-                        sg[o] = Ar * Pr - Ai * Pi;                                             // dL/dR
-                        sg[nit + o] = R * ((Ar * Pxr - Ai * Pxi) + (Pr * Axr - Pi * Axi));     // dL/dX
-                        sg[2 * nit + o] = R * ((Ar * Pzr - Ai * Pzi) + (Pr * Azr - Pi * Azi)); // dL/dZ
-                        RA[o] = make_float2(R * Ar, R * Ai);
+            for (int m = 0; m < 8; ++m) {
+                if (m < nrec) {
+                    const int a = part * nrec + m, si = a >> 1, t = t0 + (a & 1);
+                    if (act && t < T) {
+                        const float Pr = v[4 * m], Pi = v[4 * m + 1];
+                        const float Ar = v[4 * m + 2], Ai = v[4 * m + 3];
+                        const int o = (j * SB + s0 + si) * T + t;
+                        AP[o] = make_float4(Ar, Ai, Pr, Pi);
+                        sg[o] = Ar * Pr - Ai * Pi;                 // dL/dR term
                     }
                 }
             }
         }
         __syncthreads();
 
-        // 3. B_q(t, e) += sum_s R_s A_t G_e (four elements per thread, 32 apart, so that
-        // a warp reads 32 consecutive elements of a row); per-scatterer gradients of this
-        // bin tile
-        const int NC = (N + 127) >> 7;                      // chunks of 128 elements
-        for (int i = tid; i < QB * T * NC * 32; i += kGThreads) {
-            const int l = i & 31, jt = i >> 5;
-            const int jc = jt / NC, c = jt - jc * NC;
-            const int j = jc / T, t = jc - j * T;
-            const int e0 = c * 128 + l;
-            float2 b[4];
+        // 3. W and B units (one warp each)
+        for (int u = warp; u < nWB; u += kGWarps) {
+            if (u < nW) {
+                // W_e = sum_t (A_t c_te + P_t L_te) for 4 scatterers x 2 elements per lane,
+                // then Re sum_e dG_e/dX W_e and Re sum_e dG_e/dZ W_e over the warp
+                const int j = u / (SB4 * NCH), r = u - j * SB4 * NCH, s4 = r / NCH, ch = r - s4 * NCH;
+                const int s0 = 4 * s4;
+                int ec[2];
+                bool ev[2];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) b[u] = make_float2(0.f, 0.f);
-            for (int s = 0; s < SB; ++s) {
-                const float2 ra = RA[((size_t)j * SB + s) * T + t];
-                const float2 *g = Gt + ((size_t)j * SB + s) * NrG + e0;
+                for (int i = 0; i < 2; ++i) {
+                    const int e = ch * 64 + lane + 32 * i;
+                    ev[i] = e < N;
+                    ec[i] = min(e, N - 1);                  // clamped: inside the rows
+                }
+                const float4 *ap = AP + (j * SB + s0) * T;
+                const float2 *cj = cwt + (size_t)j * T * Nr, *lj = lat + (size_t)j * T * Nr;
+                float w[4][2][2];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    if (e0 + 32 * u < N) {
-                        const float2 a = g[32 * u];
-                        b[u].x = fmaf(ra.x, a.x, fmaf(-ra.y, a.y, b[u].x));
-                        b[u].y = fmaf(ra.x, a.y, fmaf(ra.y, a.x, b[u].y));
+                for (int si = 0; si < 4; ++si)
+#pragma unroll
+                    for (int i = 0; i < 2; ++i) w[si][i][0] = w[si][i][1] = 0.f;
+                for (int t = 0; t < T; ++t) {
+                    float4 a[4];
+#pragma unroll
+                    for (int si = 0; si < 4; ++si) a[si] = ap[si * T + t];
+                    const float2 c0 = cj[t * Nr + ec[0]], c1 = cj[t * Nr + ec[1]];
+                    const float2 l0 = lj[t * Nr + ec[0]], l1 = lj[t * Nr + ec[1]];
+#pragma unroll
+                    for (int si = 0; si < 4; ++si) {
+                        // (Ar, Ai, Pr, Pi) = a[si]
+                        w[si][0][0] = fmaf(a[si].x, c0.x, fmaf(-a[si].y, c0.y, fmaf(a[si].z, l0.x, fmaf(-a[si].w, l0.y, w[si][0][0]))));
+                        w[si][0][1] = fmaf(a[si].x, c0.y, fmaf(a[si].y, c0.x, fmaf(a[si].z, l0.y, fmaf(a[si].w, l0.x, w[si][0][1]))));
+                        w[si][1][0] = fmaf(a[si].x, c1.x, fmaf(-a[si].y, c1.y, fmaf(a[si].z, l1.x, fmaf(-a[si].w, l1.y, w[si][1][0]))));
+                        w[si][1][1] = fmaf(a[si].x, c1.y, fmaf(a[si].y, c1.x, fmaf(a[si].z, l1.y, fmaf(a[si].w, l1.x, w[si][1][1]))));
+                    }
+                }
+                float v[32];   // v[si]: X, v[4 + si]: Z (the rest unused)
+#pragma unroll
+                for (int si = 0; si < 4; ++si) {
+                    const size_t ro = ((size_t)j * SB + s0 + si) * NrG;
+                    float x = 0.f, z = 0.f;
+#pragma unroll
+                    for (int i = 0; i < 2; ++i) {
+                        const float2 gx = Gt[plane + ro + ec[i]], gz = Gt[2 * plane + ro + ec[i]];
+                        if (ev[i]) {
+                            x = fmaf(gx.x, w[si][i][0], fmaf(-gx.y, w[si][i][1], x));
+                            z = fmaf(gz.x, w[si][i][0], fmaf(-gz.y, w[si][i][1], z));
+                        }
+                    }
+                    v[si] = x;
+                    v[4 + si] = z;
+                }
+#pragma unroll
+                for (int o = 16; o >= 8; o >>= 1)
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+                halve_lanes<8, 4>(v, lane);
+                halve_lanes<4, 2>(v, lane);
+                halve_lanes<2, 1>(v, lane);
+                if (lane < 8) {    // lane p holds value p: X (p < 4) or Z of scatterer s0 + p mod 4
+                    const int which = lane >> 2, si = lane & 3;
+                    xz[which * QB * SB * NCH + (j * SB + s0 + si) * NCH + ch] = v[0];
+                }
+            } else {
+                // B_q(t, e) += sum_s A_t (R_s G_e) for 4 transmits x 2 elements per lane
+                const int b = u - nW, nT4 = (T + 3) >> 2;
+                const int j = b / (nT4 * NCH), r = b - j * nT4 * NCH, t4 = r / NCH, ch = r - t4 * NCH;
+                const int t0 = 4 * t4;
+                int ec[2];
+                bool ev[2];
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    const int e = ch * 64 + lane + 32 * i;
+                    ev[i] = e < N;
+                    ec[i] = min(e, N - 1);
+                }
+                int tc[4];
+#pragma unroll
+                for (int ti = 0; ti < 4; ++ti) tc[ti] = min(t0 + ti, T - 1);
+                float acc[4][2][2];
+#pragma unroll
+                for (int ti = 0; ti < 4; ++ti)
+#pragma unroll
+                    for (int i = 0; i < 2; ++i) acc[ti][i][0] = acc[ti][i][1] = 0.f;
+                for (int s = 0; s < SB; ++s) {
+                    const float R = sc[s].w;
+                    const float2 *grow = Gt + ((size_t)j * SB + s) * NrG;
+                    float2 rg[2];
+#pragma unroll
+                    for (int i = 0; i < 2; ++i) {
+                        const float2 x = grow[ec[i]];
+                        rg[i] = make_float2(R * x.x, R * x.y);
+                    }
+                    const float4 *ap = AP + (j * SB + s) * T;
+#pragma unroll
+                    for (int ti = 0; ti < 4; ++ti) {
+                        const float2 a = *reinterpret_cast<const float2 *>(ap + tc[ti]);   // A_t
+#pragma unroll
+                        for (int i = 0; i < 2; ++i) {
+                            acc[ti][i][0] = fmaf(a.x, rg[i].x, fmaf(-a.y, rg[i].y, acc[ti][i][0]));
+                            acc[ti][i][1] = fmaf(a.x, rg[i].y, fmaf(a.y, rg[i].x, acc[ti][i][1]));
+                        }
+                    }
+                }
+#pragma unroll
+                for (int ti = 0; ti < 4; ++ti) {
+                    if (t0 + ti < T) {
+                        float2 *bt = Bt + ((size_t)j * T + t0 + ti) * N;
+#pragma unroll
+                        for (int i = 0; i < 2; ++i)
+                            if (ev[i]) {
+                                bt[ec[i]].x += acc[ti][i][0];
+                                bt[ec[i]].y += acc[ti][i][1];
+                            }
                     }
                 }
             }
-            float2 *bt = Bt + ((size_t)j * T + t) * N + e0;
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-                if (e0 + 32 * u < N) { bt[32 * u].x += b[u].x; bt[32 * u].y += b[u].y; }
         }
-        if (tid < 3 * SB) {       // fixed-order sum over (bin, transmit): reproducible
+        __syncthreads();
+        if (tid < 3 * SB) {       // fixed-order sums over bins and transmits / chunks
             const int which = tid / SB, s = tid - which * SB;
             float acc = 0.f;
-            for (int j = 0; j < QB; ++j)
-                for (int t = 0; t < T; ++t) acc += sg[which * nit + (j * SB + s) * T + t];
+            if (which == 0) {
+                for (int j = 0; j < QB; ++j)
+                    for (int t = 0; t < T; ++t) acc += sg[(j * SB + s) * T + t];
+            } else {
+                const float *x = xz + (which - 1) * QB * SB * NCH;
+                for (int j = 0; j < QB; ++j)
+                    for (int ch = 0; ch < NCH; ++ch) acc += x[(j * SB + s) * NCH + ch];
+                acc *= sc[s].w;
+            }
             if (sb + s < s_end)
                 gpart[(size_t)which * n_qtiles * S + (size_t)qt * S + (sb + s)] = acc;
         }
@@ -428,13 +539,14 @@ GradGeom grad_geometry(const simus_plan *p, int T, int64_t S) {
     GradGeom g{};
     g.ok = (int64_t)T * p->N <= 2048;
     g.n_qtiles = (p->nq + kGQB - 1) / kGQB;
-    const size_t Nr = (size_t)p->N + 1;
     const int tab_full = (p->d_dtab && p->delta_table && !p->probe.two_d) ? p->gc.tab_n : 0;
     auto smem_for = [&](int SB, int tab_n) {
-        return sizeof(float4) * kGSBMax + sizeof(SubElem) * p->M
-             + sizeof(float2) * (size_t)kGQB * T * Nr * 2 + sizeof(float2) * (size_t)kGQB * T * p->N
-             + sizeof(float2) * (size_t)3 * kGQB * SB * grad_row(p->N, grad_ks(SB, T))
-             + sizeof(float2) * (size_t)kGQB * SB * T + sizeof(float) * 3 * kGQB * SB * T
+        const size_t nit = (size_t)kGQB * SB * T, nch = (size_t)(p->N + 63) / 64;
+        return sizeof(float4) * kGSBMax + sizeof(SubElem) * p->M + sizeof(float4) * nit
+             + sizeof(float2) * (size_t)kGQB * T * grad_wrow(p->N) * 2
+             + sizeof(float2) * (size_t)kGQB * T * p->N
+             + sizeof(float2) * (size_t)3 * kGQB * SB * grad_row(p->N)
+             + sizeof(float) * nit + sizeof(float) * ((2 * kGQB * SB * nch + 3) & ~(size_t)3)
              + 2 * sizeof(float4) * (size_t)tab_n;
     };
     // 16-scatterer groups with the delta table, else without it, else 8-scatterer groups
