@@ -134,7 +134,7 @@ TcShape tc_shape(const simus_plan *p, int T, int64_t S, double work_share, int i
                     if (nN > 256 || nN + stash > 512) continue;   // (an M = 128 MMA takes N <= 256)
                     const int qb = (512 - nN - stash) / (nN * G * g.mh);
                     if (qb < per) continue;
-                    const size_t sm = unit_smem(g.Np, nN, nbuf, p->M, tab_n, split);
+                    const size_t sm = unit_smem(g.Np, nN, nbuf, p->M + p->nu, tab_n, split);
                     if (sm > limit) continue;
                     g.ok = true;
                     g.TG = TG; g.nN = nN; g.pair = per - 1; g.nbuf = nbuf; g.n_groups = G;

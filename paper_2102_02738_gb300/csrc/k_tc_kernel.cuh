@@ -165,6 +165,201 @@ __device__ __forceinline__ void gen_two(const GreenConst &gc, const float4 *sub,
     }
 }
 
+// Packed FP32 pairs (f32x2 instructions, one issue slot for both halves): gen_two2 keeps
+// the two element chains of gen_two in the .x and .y halves.
+__device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+
+// Sub-element records of element pairs for gen_two2 (Y = 0): pair p = elements 2p, 2p + 1
+// (the last element repeated for odd N), sub-element mu at [2 (p nu + mu)], two float4 with
+// the pair's values side by side: linear arrays (-x_h, -x_h', -x_l, -x_l'), (0, 0, 0, 0);
+// convex arrays (cos psi, cos psi', sin psi, sin psi'), (-l0, -l0', -z0, -z0').
+__device__ __forceinline__ void paired_sub(const SubElem &a, const SubElem &b, bool linear,
+                                           float4 &A, float4 &B) {
+    if (linear) {
+        A = make_float4(-a.xh, -b.xh, -a.xl, -b.xl);
+        B = make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+        A = make_float4(a.cpsi, b.cpsi, a.spsi, b.spsi);
+        B = make_float4(-a.l0, -b.l0, -a.z0, -b.z0);
+    }
+}
+
+// sinc(x) of both halves by the short fits (MODE 1, 2); MODE 0 per half.
+template <int MODE>
+__device__ __forceinline__ float2 sinc_short2(float2 x) {
+    if (MODE == 1) {
+        const float2 s = mul2(x, x);
+        float2 p = fma2(dup2(2.1803757591e-06f), s, dup2(-1.9345620240e-04f));
+        p = fma2(p, s, dup2(8.3155957982e-03f));
+        p = fma2(p, s, dup2(-1.6664430499e-01f));
+        return fma2(p, s, dup2(9.9999547005e-01f));
+    }
+    if (MODE == 2) {
+        const float2 s = mul2(x, x);
+        float2 p = fma2(dup2(-1.6607067721e-08f), s, dup2(2.5681124498e-06f));
+        p = fma2(p, s, dup2(-1.9642902771e-04f));
+        p = fma2(p, s, dup2(8.3237346262e-03f));
+        p = fma2(p, s, dup2(-1.6664959490e-01f));
+        return fma2(p, s, dup2(9.9999505281e-01f));
+    }
+    return make_float2(sinc_short<0>(x.x), sinc_short<0>(x.y));
+}
+
+// gen_two at Y = 0 with the two chains as packed pairs: the same geometry (FP32 local
+// coordinates, one Newton step on r, exact double-float phase rate), phase seed and
+// phasor recurrence, sinc fit and delta table, each FP32 operation of both chains one
+// f32x2 instruction; the SFU operations, the table pieces (rows differ per chain) and the
+// range checks stay per chain.  sub: paired records (paired_sub).
+template <int NB, bool TAB, int SINC, bool LINEAR>
+__device__ __forceinline__ void gen_two2(const GreenConst &gc, const float4 *sub,
+                                         const float4 *tabs, const float4 &ps, int e0, float qA,
+                                         float2 (&ore)[NB], float2 (&oim)[NB]) {
+    const int N = gc.N, nu = gc.nu;
+    const float2 wv = make_float2(e0 < N ? 1.0f : 0.0f, e0 + 1 < N ? 1.0f : 0.0f);
+    const int pb = (min(e0, N - 1) >> 1) * nu;
+    const float t0 = gc.tab_x0 * gc.tab_inv_dx, tmax = (float)gc.tab_n - 0.5f;
+#pragma unroll
+    for (int b = 0; b < NB; ++b) ore[b] = oim[b] = make_float2(0.0f, 0.0f);
+    const float2 xs2 = dup2(ps.x), zs2 = dup2(ps.z);
+    for (int mu = 0; mu < nu; ++mu) {
+        const float4 A = sub[2 * (pb + mu)];
+        float2 lx, lz;
+        if (LINEAR) {
+            lx = add2(add2(xs2, make_float2(A.x, A.y)), make_float2(A.z, A.w));
+            lz = zs2;
+        } else {
+            const float4 B = sub[2 * (pb + mu) + 1];
+            const float2 cp = make_float2(A.x, A.y), sp = make_float2(A.z, A.w);
+            lx = fma2(xs2, cp, fma2(dup2(-ps.z), sp, make_float2(B.x, B.y)));
+            lz = fma2(xs2, sp, fma2(zs2, cp, make_float2(B.z, B.w)));
+        }
+        float2 r2 = fma2(lx, lx, mul2(lz, lz));
+        const bool v0 = r2.x > 1e-24f, v1 = r2.y > 1e-24f;   // a scatterer on a centroid is dropped
+        if (!v0) r2.x = 1.0f;
+        if (!v1) r2.y = 1.0f;
+        const float2 rr = make_float2(rsqrt_a(r2.x), rsqrt_a(r2.y));
+        const float2 r0 = mul2(r2, rr);
+        const float2 rh = fma2(fma2(neg2(r0), r0, r2), mul2(dup2(0.5f), rr), r0);
+        const float2 uh = mul2(rh, dup2(gc.Kh));
+        const float2 ul = fma2(rh, dup2(gc.Kl), fma2(rh, dup2(gc.Kh), neg2(uh)));
+        const float2 sin_t = mul2(lx, rr), cos_t = mul2(lz, rr);
+        float2 ob = gc.baffle == SIMUS_BAFFLE_SOFT ? cos_t
+                  : (gc.baffle == SIMUS_BAFFLE_RIGID ? dup2(1.0f)
+                     : make_float2(cos_t.x / (cos_t.x + gc.zeta), cos_t.y / (cos_t.y + gc.zeta)));
+        if (!(cos_t.x > 0.0f) || !v0) ob.x = 0.0f;          // behind the aperture (Eq. 39 reading)
+        if (!(cos_t.y > 0.0f) || !v1) ob.y = 0.0f;
+        const float2 ea = mul2(dup2(-qA * gc.att2), rh);
+        const float2 a1 = gc.two_d ? make_float2(rsqrt_a(rh.x), rsqrt_a(rh.y)) : mul2(dup2(gc.h), rr);
+        const float2 amp0 = mul2(mul2(mul2(a1, ob), make_float2(ex2_a(ea.x), ex2_a(ea.y))), wv);
+        const float2 sa = mul2(dup2(-gc.att2), rh);
+        const float2 mstep = make_float2(ex2_a(sa.x), ex2_a(sa.y));
+        const float2 xb = mul2(dup2(gc.k1b), sin_t);
+        const float2 kap = mul2(dup2(gc.kh * gc.h2), add2(dup2(gc.inv_rf), neg2(rr)));
+
+        float2 kt = make_float2(0.f, 0.f), u = make_float2(0.f, 0.f), tq = make_float2(0.f, 0.f);
+        int ti[2] = {0, 0};
+        bool ok = TAB, far = false;
+        if (TAB) {
+            kt = mul2(kap, dup2(gc.tab_inv_dx));
+            tq = fma2(dup2(qA), kt, dup2(-t0));
+            const float fl0 = floorf(fminf(fmaxf(tq.x, 0.0f), tmax));
+            const float fl1 = floorf(fminf(fmaxf(tq.y, 0.0f), tmax));
+            ti[0] = (int)fl0;
+            ti[1] = (int)fl1;
+            u = add2(tq, make_float2(-fl0, -fl1));
+            const float2 ue = fma2(dup2((float)(NB - 1)), kt, u);   // the last bin's u
+            ok = u.x >= 0.0f && u.x <= 1.0f && u.y >= 0.0f && u.y <= 1.0f;
+            far = !(ue.x >= -0.5f && ue.x <= 1.5f) || !(ue.y >= -0.5f && ue.y <= 1.5f);
+        }
+        float4 lo[2], hi[2];
+        if (TAB) {
+#pragma unroll
+            for (int c = 0; c < 2; ++c) { lo[c] = tabs[2 * ti[c]]; hi[c] = tabs[2 * ti[c] + 1]; }
+        }
+        // phase seed at the first bin (exact reduction of q u), then the phasor step
+        float2 zr, zi, wr = make_float2(0.f, 0.f), wi = make_float2(0.f, 0.f);
+        {
+            const float2 q2 = dup2(qA);
+            const float2 a = mul2(q2, uh);
+            const float2 e = fma2(q2, ul, fma2(q2, uh, neg2(a)));
+            const float2 fr = add2(add2(a, make_float2(-rintf(a.x), -rintf(a.y))), e);
+            const float2 ph = mul2(dup2(6.283185307179586f), fr);
+            float2 sn, cs;
+            sincos_a(ph.x, sn.x, cs.x);
+            sincos_a(ph.y, sn.y, cs.y);
+            zr = mul2(amp0, cs);
+            zi = mul2(amp0, sn);
+            if (NB > 1) {
+                const float2 fu = add2(add2(uh, make_float2(-rintf(uh.x), -rintf(uh.y))), ul);
+                const float2 ps2 = mul2(dup2(6.283185307179586f), fu);
+                sincos_a(ps2.x, sn.x, cs.x);
+                sincos_a(ps2.y, sn.y, cs.y);
+                wr = mul2(mstep, cs);
+                wi = mul2(mstep, sn);
+            }
+        }
+        float2 er[NB], ei[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const float2 m = sinc_short2<SINC>(mul2(dup2(qA + (float)b), xb));
+            er[b] = mul2(zr, m);
+            ei[b] = mul2(zi, m);
+            if (b + 1 < NB) {
+                const float2 nzr = fma2(zr, wr, neg2(mul2(zi, wi)));
+                zi = fma2(zr, wi, mul2(zi, wr));
+                zr = nzr;
+            }
+        }
+        float2 d[2][NB];
+        if (TAB) {
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                const float2 ub = fma2(dup2((float)b), kt, u);
+                d[0][b] = cubic_piece(lo[0], hi[0], ub.x);
+                d[1][b] = cubic_piece(lo[1], hi[1], ub.y);
+            }
+        }
+        if (TAB && NB > 1 && far) {
+            // a later bin moved more than half an interval past its piece (scatterers a few
+            // mm from the sub-element): it takes its own piece
+#pragma unroll
+            for (int c = 0; c < 2; ++c)
+#pragma unroll
+                for (int b = 1; b < NB; ++b) {
+                    const float ktc = c ? kt.y : kt.x, uc = c ? u.y : u.x, tqc = c ? tq.y : tq.x;
+                    const float ub = fmaf((float)b, ktc, uc);
+                    if (!(ub >= -0.5f && ub <= 1.5f)) {
+                        const float tb = fmaf((float)b, ktc, tqc);
+                        const float fl = floorf(fminf(fmaxf(tb, 0.0f), tmax));
+                        const int i = (int)fl;
+                        const float v = tb - fl;
+                        d[c][b] = cubic_piece(tabs[2 * i], tabs[2 * i + 1], v);
+                        ok = ok && v >= 0.0f && v <= 1.0f;
+                    }
+                }
+        }
+        if (!ok) {   // outside the table (within ~2 mm of the sub-element): Eq. 16 directly
+            PairSetup P;
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                P.kap = c ? kap.y : kap.x;
+#pragma unroll
+                for (int b = 0; b < NB; ++b) d[c][b] = delta_f<false>(gc, P, qA + (float)b);
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const float2 dre = make_float2(d[0][b].x, d[1][b].x), dim = make_float2(d[0][b].y, d[1][b].y);
+            ore[b] = fma2(er[b], dre, fma2(neg2(ei[b]), dim, ore[b]));
+            oim[b] = fma2(er[b], dim, fma2(ei[b], dre, oim[b]));
+        }
+    }
+}
+
 // One generation pass over a scatterer tile: every (scatterer, group of 8 elements) item
 // at bins qA .. qA + NB - 1.  Bin 0 goes as FP16/BF16 rows of the K-major tile A0, bin 1
 // to A1 when there are two shared-memory tile buffers (nbuf = 2); every further bin goes
@@ -190,7 +385,17 @@ __device__ __forceinline__ void gen_tiles(const GreenConst &gc, const float4 *su
 #pragma unroll
         for (int jp = 0; jp < 4; ++jp) {
             float o[2][NB][2];
-            gen_two<NB, TAB, HAS_Y, SINC, LINEAR>(gc, sub, tabs, ps, eg * 8 + 2 * jp, qA, o);
+            if (HAS_Y) {
+                gen_two<NB, TAB, HAS_Y, SINC, LINEAR>(gc, sub, tabs, ps, eg * 8 + 2 * jp, qA, o);
+            } else {
+                float2 ore[NB], oim[NB];
+                gen_two2<NB, TAB, SINC, LINEAR>(gc, sub, tabs, ps, eg * 8 + 2 * jp, qA, ore, oim);
+#pragma unroll
+                for (int b = 0; b < NB; ++b) {
+                    o[0][b][0] = ore[b].x; o[1][b][0] = ore[b].y;
+                    o[0][b][1] = oim[b].x; o[1][b][1] = oim[b].y;
+                }
+            }
 #pragma unroll
             for (int b = 0; b < NB; ++b) {
                 if (split) {
@@ -351,8 +556,8 @@ k_tc_rf(const TcUnit *__restrict__ units, int n_units, int64_t n_items, int *cou
         const uint32_t b1_part = (uint32_t)nN * K1 * 2, b2_part = (uint32_t)nN * 256 * 2;
         unsigned char *B2 = B1 + (size_t)nops * b1_part;
         float4 *sc = reinterpret_cast<float4 *>(B2 + (size_t)nops * b2_part);
-        float4 *sub = sc + kSB;                                            // compact records
-        float4 *tabs = sub + M;                                            // delta table
+        float4 *sub = sc + kSB;        // compact records (Y != 0) or paired records (Y = 0)
+        float4 *tabs = sub + M + gc.nu;                                    // delta table
         const bool use_tab = !HAS_Y && gc.tab_n > 0;
         const uint32_t abuf0 = tc::smem_u32(A0), abuf1 = tc::smem_u32(A1);
         const uint32_t b1s = tc::smem_u32(B1), b2s = tc::smem_u32(B2);
@@ -360,7 +565,16 @@ k_tc_rf(const TcUnit *__restrict__ units, int n_units, int64_t n_items, int *cou
         const uint32_t idesc2 = idesc1 | (1u << 15) | (1u << 16);   // A and B MN-major
         const uint32_t b1_bytes = nops * b1_part;
         if (ui != cur_unit) {
-            for (int i = tid; i < M; i += kThreads) sub[i] = compact_sub(U.sub[i], LINEAR);
+            if (HAS_Y) {
+                for (int i = tid; i < M; i += kThreads) sub[i] = compact_sub(U.sub[i], LINEAR);
+            } else {
+                const int nu = gc.nu, np = ((N + 1) >> 1) * nu;
+                for (int i = tid; i < np; i += kThreads) {
+                    const int pp = i / nu, mu = i - pp * nu;
+                    const int ea = min(2 * pp, N - 1), eb = min(2 * pp + 1, N - 1);
+                    paired_sub(U.sub[ea * nu + mu], U.sub[eb * nu + mu], LINEAR, sub[2 * i], sub[2 * i + 1]);
+                }
+            }
             if (use_tab)
                 for (int i = tid; i < 2 * gc.tab_n; i += kThreads) tabs[i] = U.dtab[i];
             cur_unit = ui;
