@@ -122,6 +122,173 @@ k_adjoint_dft(const float *__restrict__ drf, int N, int n_chan, int nq, int q_lo
     }
 }
 
+// ---------------------------------------------------------------------------------
+// Generation of two elements at once (delta table, Y = 0): elements 2p and 2p + 1 of a
+// scatterer in the .x and .y halves of packed FP32 pairs (green.cuh), the same
+// double-float geometry, phase reduction and derivative terms as pair_setup, pair_grad
+// and green_grad_assemble, each FP32 operation of both one f32x2 instruction; the SFU
+// operations, the table pieces (rows differ per element) and the direct-delta fallback stay
+// per element.  Sub-element records of element pairs, pair p and sub-element mu at
+// [3 (p nu + mu)]: (x_h, x_h', x_l, x_l'), (z_h, z_h', z_l, z_l'), (cos psi, cos psi',
+// sin psi, sin psi'), the last element repeated for odd N.
+__device__ __forceinline__ float2 sinc_poly32_2(float2 x) {
+    const float2 s = mul2(x, x);
+    float2 p = fma2(dup2(1.3530106150e-10f), s, dup2(-2.4705910363e-08f));
+    p = fma2(p, s, dup2(2.7533500506e-06f));
+    p = fma2(p, s, dup2(-1.9840424160e-04f));
+    p = fma2(p, s, dup2(8.3333190001e-03f));
+    p = fma2(p, s, dup2(-1.6666665754e-01f));
+    return fma2(p, s, dup2(9.9999999903e-01f));
+}
+__device__ __forceinline__ float2 dsinc_poly2(float2 x) {   // 2 x p'(x^2), as dsinc_poly
+    const float2 s = mul2(x, x);
+    float2 p = fma2(dup2(6.0f * 1.3530106150e-10f), s, dup2(5.0f * -2.4705910363e-08f));
+    p = fma2(p, s, dup2(4.0f * 2.7533500506e-06f));
+    p = fma2(p, s, dup2(3.0f * -1.9840424160e-04f));
+    p = fma2(p, s, dup2(2.0f * 8.3333190001e-03f));
+    p = fma2(p, s, dup2(-1.6666665754e-01f));
+    return mul2(mul2(dup2(2.0f), x), p);
+}
+
+template <bool NARROW>
+__device__ __forceinline__ void grad_gen_pair(const GreenConst &gc, const float4 *subP,
+                                              const float4 *tabs, float xs, float zs, int p,
+                                              float q0, float2 (&Gr)[kGQB], float2 (&Gi)[kGQB],
+                                              float2 (&Xr)[kGQB], float2 (&Xi)[kGQB],
+                                              float2 (&Zr)[kGQB], float2 (&Zi)[kGQB]) {
+    const int nu = gc.nu;
+    const float t0 = gc.tab_x0 * gc.tab_inv_dx, tmax = (float)gc.tab_n - 0.5f;
+    const float cdx = gc.tab_inv_dx * gc.kh * gc.h2;           // dx/dr per bin times r^2
+#pragma unroll
+    for (int j = 0; j < kGQB; ++j)
+        Gr[j] = Gi[j] = Xr[j] = Xi[j] = Zr[j] = Zi[j] = make_float2(0.f, 0.f);
+    const float2 xs2 = dup2(xs), zs2 = dup2(zs);
+    for (int mu = 0; mu < nu; ++mu) {
+        const float4 RA = subP[3 * (p * nu + mu)], RB = subP[3 * (p * nu + mu) + 1],
+                     RC = subP[3 * (p * nu + mu) + 2];
+        const float2 xh = make_float2(RA.x, RA.y), xl = make_float2(RA.z, RA.w);
+        const float2 zh = make_float2(RB.x, RB.y), zl = make_float2(RB.z, RB.w);
+        const float2 cp = make_float2(RC.x, RC.y), sp = make_float2(RC.z, RC.w);
+        // pair_setup: double-float distance and phase rate
+        const df2x dx = df_sub_f2(xs2, xh, xl), dz = df_sub_f2(zs2, zh, zl);
+        df2x r2 = df_add2(df_sqr2(dx), df_sqr2(dz));
+        const bool v0 = r2.h.x > 1e-24f, v1 = r2.h.y > 1e-24f;   // on a centroid: dropped
+        if (!v0) { r2.h.x = 1.0f; r2.l.x = 0.0f; }
+        if (!v1) { r2.h.y = 1.0f; r2.l.y = 0.0f; }
+        const float2 rr = make_float2(rsqrt_a(r2.h.x), rsqrt_a(r2.h.y));
+        const float2 rh0 = mul2(r2.h, rr);
+        const float2 rl0 = mul2(add2(fma2(neg2(rh0), rh0, r2.h), r2.l), mul2(dup2(0.5f), rr));
+        const df2x r = fast_two_sum2(rh0, rl0);
+        const df2x u = df_mul2(r, df2x{dup2(gc.Kh), dup2(gc.Kl)});
+        const float2 lx = fma2(dx.h, cp, neg2(mul2(dz.h, sp))), lz = fma2(dx.h, sp, mul2(dz.h, cp));
+        const float2 sin_t = mul2(lx, rr), cos_t = mul2(lz, rr);
+        float2 ob0 = gc.baffle == SIMUS_BAFFLE_SOFT ? cos_t
+                   : (gc.baffle == SIMUS_BAFFLE_RIGID ? dup2(1.0f)
+                      : make_float2(cos_t.x / (cos_t.x + gc.zeta), cos_t.y / (cos_t.y + gc.zeta)));
+        if (!(cos_t.x > 0.0f) || !v0) ob0.x = 0.0f;        // behind the aperture (Eq. 39 reading)
+        if (!(cos_t.y > 0.0f) || !v1) ob0.y = 0.0f;
+        const float2 sa = mul2(dup2(-gc.att2), r.h);
+        const float2 mstep = make_float2(ex2_a(sa.x), ex2_a(sa.y));
+        const float2 xb = mul2(dup2(gc.k1b), sin_t);
+        const float2 kap = mul2(dup2(gc.kh * gc.h2), sub2(dup2(gc.inv_rf), rr));
+        // pair_grad: FP32 offsets and the derivatives of r, sin and cos theta
+        const float2 dxf = sub2(sub2(xs2, xh), xl), dzf = sub2(sub2(zs2, zh), zl);
+        const float2 lx2 = fma2(dxf, cp, neg2(mul2(dzf, sp))), lz2 = fma2(dxf, sp, mul2(dzf, cp));
+        const float2 st = mul2(lx2, rr), ct = mul2(lz2, rr);
+        const float2 drdx = mul2(dxf, rr), drdz = mul2(dzf, rr);
+        const float2 dsdx = mul2(fma2(neg2(st), drdx, cp), rr);
+        const float2 dcdx = mul2(fma2(neg2(ct), drdx, sp), rr);
+        const float2 dsdz = mul2(fma2(neg2(st), drdz, neg2(sp)), rr);
+        const float2 dcdz = mul2(fma2(neg2(ct), drdz, cp), rr);
+        float2 ob, dob;
+        if (gc.baffle == SIMUS_BAFFLE_SOFT) {
+            ob = ct;
+            dob = dup2(1.0f);
+        } else if (gc.baffle == SIMUS_BAFFLE_RIGID) {
+            ob = dup2(1.0f);
+            dob = dup2(0.0f);
+        } else {
+            const float d0 = 1.0f / (ct.x + gc.zeta), d1 = 1.0f / (ct.y + gc.zeta);
+            ob = make_float2(ct.x * d0, ct.y * d1);
+            dob = make_float2(gc.zeta * d0 * d0, gc.zeta * d1 * d1);
+        }
+        if (!(ct.x > 0.0f) || !(ob0.x != 0.0f)) { ob.x = 0.0f; dob.x = 0.0f; }
+        if (!(ct.y > 0.0f) || !(ob0.y != 0.0f)) { ob.y = 0.0f; dob.y = 0.0f; }
+        const float2 rr2 = mul2(rr, rr);
+        // bins: E = exp((i k - k_a) r) / r (the obliquity kept apart), phase reduced exactly
+        // at every bin, absorption stepped by exp(-k_a r df / c)
+        const float2 ea = mul2(dup2(-q0 * gc.att2), r.h);
+        float2 amp = mul2(mul2(dup2(gc.h), rr), make_float2(ex2_a(ea.x), ex2_a(ea.y)));
+        const float2 kt = mul2(kap, dup2(gc.tab_inv_dx));
+        const float2 dxdr = mul2(dup2(cdx), rr2);
+#pragma unroll
+        for (int j = 0; j < kGQB; ++j) {
+            const float q = q0 + (float)j;
+            if (j > 0) amp = mul2(amp, mstep);
+            const float2 ph = mul2(dup2(6.283185307179586f), df_frac_mul2(dup2(q), u));
+            float2 sn, cs;
+            sincos_a(ph.x, sn.x, cs.x);
+            sincos_a(ph.y, sn.y, cs.y);
+            const float2 Er = mul2(amp, cs), Ei = mul2(amp, sn);
+            // delta / h and d(delta / h)/dr per element: the table piece, else Eq. 16-18
+            const float2 tt = fma2(dup2(q), kt, dup2(-t0));
+            float dv[2][4];
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const float tc = c ? tt.y : tt.x;
+                const float fl = floorf(fminf(fmaxf(tc, 0.0f), tmax));
+                const int i = (int)fl;
+                const float uu = tc - fl;
+                if (uu >= 0.0f && uu <= 1.0f) {
+                    const float4 lo = tabs[2 * i], hi = tabs[2 * i + 1];
+                    const float2 d = cubic_piece(lo, hi, uu);
+                    const float sc = q * (c ? dxdr.y : dxdr.x);
+                    dv[c][0] = d.x;
+                    dv[c][1] = d.y;
+                    dv[c][2] = fmaf(uu, fmaf(3.0f * uu, hi.z, 2.0f * hi.x), lo.z) * sc;
+                    dv[c][3] = fmaf(uu, fmaf(3.0f * uu, hi.w, 2.0f * hi.y), lo.w) * sc;
+                } else {
+                    PairSetup P;
+                    PairGrad Q;
+                    P.kap = c ? kap.y : kap.x;
+                    Q.rr2 = c ? rr2.y : rr2.x;
+                    delta_and_dr(gc, P, Q, q, dv[c][0], dv[c][1], dv[c][2], dv[c][3]);
+                }
+            }
+            const float2 dr = make_float2(dv[0][0], dv[1][0]), di = make_float2(dv[0][1], dv[1][1]);
+            const float2 ddr = make_float2(dv[0][2], dv[1][2]), ddi = make_float2(dv[0][3], dv[1][3]);
+            // green_grad_assemble
+            const float2 x = mul2(dup2(q), xb);
+            float2 scv, dsc;
+            if (NARROW) {
+                scv = sinc_poly32_2(x);
+                dsc = dsinc_poly2(x);
+            } else {
+                scv = make_float2(sinc_f<0>(x.x), sinc_f<0>(x.y));
+                dsc = make_float2(dsinc_wide(x.x), dsinc_wide(x.y));
+            }
+            const float2 D = mul2(scv, ob);
+            const float2 dDs = mul2(mul2(dsc, dup2(q * gc.k1b)), ob), dDc = mul2(scv, dob);
+            const float2 dDx = fma2(dDs, dsdx, mul2(dDc, dcdx));
+            const float2 dDz = fma2(dDs, dsdz, mul2(dDc, dcdz));
+            // d/dr of exp(-k_a r) / r: -k_a - 1/r (3-D)
+            const float2 a = sub2(dup2(-q * gc.att2 * 0.69314718055994531f), rr);
+            const float bq = q * gc.k1;
+            const float2 Qr = add2(fma2(a, dr, mul2(dup2(-bq), di)), ddr);
+            const float2 Qi = add2(fma2(a, di, mul2(dup2(bq), dr)), ddi);
+            const float2 Vr = fma2(Er, dr, neg2(mul2(Ei, di))), Vi = fma2(Er, di, mul2(Ei, dr));
+            const float2 Wr = fma2(Er, Qr, neg2(mul2(Ei, Qi))), Wi = fma2(Er, Qi, mul2(Ei, Qr));
+            const float2 Dx = mul2(D, drdx), Dz = mul2(D, drdz);
+            Gr[j] = fma2(Vr, D, Gr[j]);
+            Gi[j] = fma2(Vi, D, Gi[j]);
+            Xr[j] = fma2(Wr, Dx, fma2(Vr, dDx, Xr[j]));
+            Xi[j] = fma2(Wi, Dx, fma2(Vi, dDx, Xi[j]));
+            Zr[j] = fma2(Wr, Dz, fma2(Vr, dDz, Zr[j]));
+            Zi[j] = fma2(Wi, Dz, fma2(Vi, dDz, Zi[j]));
+        }
+    }
+}
+
 // Shared-memory rows of N complex values are padded to Nr = N + 1 (weights, adjoint
 // spectra) or NrG (Green's tiles) so that rows of different transmits or scatterers start
 // in different banks.  The sub-element records are held as two float4 planes indexed
@@ -150,7 +317,7 @@ k_grad(const GreenConst gc, const SubElem *__restrict__ sub_g, const float *__re
     float4 *sc = reinterpret_cast<float4 *>(smem_raw);              // [SB] (x, 0, z, R)
     float4 *subA = sc + kGSBMax;                                     // [nu][N] xh, xl, zh, zl
     float4 *subB = subA + M;                                        // [nu][N] cpsi, spsi, l0, z0
-    float4 *AP = subB + M;                                          // [QB][SB][T] (A_t, P_t)
+    float4 *AP = subB + M + 3 * nu;                                 // [QB][SB][T] (A_t, P_t)
     float2 *cwt = reinterpret_cast<float2 *>(AP + nit);             // [QB][T][Nr]
     float2 *lat = cwt + QB * T * Nr;                                // [QB][T][Nr]
     float2 *Bt = lat + QB * T * Nr;                                 // [QB][T][N]
@@ -166,11 +333,22 @@ k_grad(const GreenConst gc, const SubElem *__restrict__ sub_g, const float *__re
 
     if (TAB)
         for (int i = tid; i < 2 * gc.tab_n; i += kGThreads) tabs[i] = dtab[i];
-    for (int i = tid; i < M; i += kGThreads) {          // global [e][mu] -> shared [mu][e]
-        const float4 *r = reinterpret_cast<const float4 *>(sub_g + i);
-        const int e = i / nu, mu = i - e * nu;
-        subA[mu * N + e] = r[0];
-        subB[mu * N + e] = r[1];
+    if (TAB) {          // element-pair records for grad_gen_pair (in place of the planes)
+        const int np = ((N + 1) >> 1) * nu;
+        for (int i = tid; i < np; i += kGThreads) {
+            const int pp = i / nu, mu = i - pp * nu;
+            const SubElem a = sub_g[min(2 * pp, N - 1) * nu + mu], b = sub_g[min(2 * pp + 1, N - 1) * nu + mu];
+            subA[3 * i] = make_float4(a.xh, b.xh, a.xl, b.xl);
+            subA[3 * i + 1] = make_float4(a.zh, b.zh, a.zl, b.zl);
+            subA[3 * i + 2] = make_float4(a.cpsi, b.cpsi, a.spsi, b.spsi);
+        }
+    } else {
+        for (int i = tid; i < M; i += kGThreads) {      // global [e][mu] -> shared [mu][e]
+            const float4 *r = reinterpret_cast<const float4 *>(sub_g + i);
+            const int e = i / nu, mu = i - e * nu;
+            subA[mu * N + e] = r[0];
+            subB[mu * N + e] = r[1];
+        }
     }
     for (int i = tid; i < QB * T * N; i += kGThreads) {
         int j = i / (T * N), r = i - j * T * N, t = r / N, e = r - t * N, k = k0 + j;
@@ -197,8 +375,31 @@ k_grad(const GreenConst gc, const SubElem *__restrict__ sub_g, const float *__re
         }
         __syncthreads();
 
-        // 1. G, dG/dX, dG/dZ tiles
-        for (int pr = tid; pr < SB * N; pr += kGThreads) {
+        // 1. G, dG/dX, dG/dZ tiles: two elements per item with the delta table
+        if (TAB) {
+            const int NP = (N + 1) >> 1;
+            for (int pr = tid; pr < SB * NP; pr += kGThreads) {
+                const int s = pr / NP, pp = pr - s * NP;
+                const float4 ps = sc[s];
+                float2 Gr[QB], Gi[QB], Xr[QB], Xi[QB], Zr[QB], Zi[QB];
+                grad_gen_pair<NARROW>(gc, subA, tabs, ps.x, ps.z, pp, q0, Gr, Gi, Xr, Xi, Zr, Zi);
+                const int e0 = 2 * pp;
+#pragma unroll
+                for (int j = 0; j < QB; ++j) {
+                    const size_t o = ((size_t)j * SB + s) * NrG + e0;
+                    if (e0 + 1 < N) {   // (o even: 16-byte stores of both elements)
+                        *reinterpret_cast<float4 *>(Gt + o) = make_float4(Gr[j].x, Gi[j].x, Gr[j].y, Gi[j].y);
+                        *reinterpret_cast<float4 *>(Gt + plane + o) = make_float4(Xr[j].x, Xi[j].x, Xr[j].y, Xi[j].y);
+                        *reinterpret_cast<float4 *>(Gt + 2 * plane + o) = make_float4(Zr[j].x, Zi[j].x, Zr[j].y, Zi[j].y);
+                    } else {
+                        Gt[o] = make_float2(Gr[j].x, Gi[j].x);
+                        Gt[plane + o] = make_float2(Xr[j].x, Xi[j].x);
+                        Gt[2 * plane + o] = make_float2(Zr[j].x, Zi[j].x);
+                    }
+                }
+            }
+        }
+        for (int pr = tid; pr < (TAB ? 0 : SB * N); pr += kGThreads) {
             const int s = pr / N, e = pr - s * N;
             const float4 ps = sc[s];
             float2 G[QB], GX[QB], GZ[QB];
@@ -542,7 +743,8 @@ GradGeom grad_geometry(const simus_plan *p, int T, int64_t S) {
     const int tab_full = (p->d_dtab && p->delta_table && !p->probe.two_d) ? p->gc.tab_n : 0;
     auto smem_for = [&](int SB, int tab_n) {
         const size_t nit = (size_t)kGQB * SB * T, nch = (size_t)(p->N + 63) / 64;
-        return sizeof(float4) * kGSBMax + sizeof(SubElem) * p->M + sizeof(float4) * nit
+        return sizeof(float4) * kGSBMax + sizeof(SubElem) * p->M + 3 * sizeof(float4) * p->nu
+             + sizeof(float4) * nit
              + sizeof(float2) * (size_t)kGQB * T * grad_wrow(p->N) * 2
              + sizeof(float2) * (size_t)kGQB * T * p->N
              + sizeof(float2) * (size_t)3 * kGQB * SB * grad_row(p->N)

@@ -165,13 +165,8 @@ __device__ __forceinline__ void gen_two(const GreenConst &gc, const float4 *sub,
     }
 }
 
-// Packed FP32 pairs (f32x2 instructions, one issue slot for both halves): gen_two2 keeps
-// the two element chains of gen_two in the .x and .y halves.
-__device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
-__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+// gen_two2 keeps the two element chains of gen_two in the .x and .y halves of packed
+// FP32 pairs (green.cuh).
 
 // Sub-element records of element pairs for gen_two2 (Y = 0): pair p = elements 2p, 2p + 1
 // (the last element repeated for odd N), sub-element mu at [2 (p nu + mu)], two float4 with
