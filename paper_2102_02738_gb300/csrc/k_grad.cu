@@ -28,6 +28,9 @@ namespace {
 constexpr int kGThreads = 384;  // 12 warps: the register budget of the generation allows it
 constexpr int kGWarps = kGThreads / 32;
 constexpr int kGQB = 2;     // bins per tile
+// the Green's tiles follow QB T N complex values of B and take 16-byte stores of element
+// pairs: an even QB keeps them on a 16-byte boundary for every T and N
+static_assert(kGQB % 2 == 0, "k_grad's Green's tiles need an even number of bins per tile");
 constexpr int kGSBMax = 16; // scatterers per group (16, or 8 where shared memory is short)
 
 // P, A products: an item is (bin, 4 scatterers, 2 transmits) with both weight sets (32
