@@ -31,6 +31,58 @@ constexpr int kMtQBMax = 4;     // bins per tile (4, or 2 for many transmits)
 constexpr int kMtSBMax = 32;    // scatterers per group (32, 16 or 8: what shared memory allows)
 }  // namespace
 
+// Green's terms of elements 2p and 2p + 1 of one scatterer at the QB bins (Y = 0), the two
+// elements in the .x and .y halves of packed FP32 pairs (pair_setup2): the phase reduced
+// exactly at every bin, the absorption stepped per bin, delta per element (table piece or
+// Eq. 16).  Gr[j], Gi[j]: (Re, Re') and (Im, Im') of G_e at bin q0 + j.
+template <int QB, int SINC, bool TAB>
+__device__ __forceinline__ void mt_gen_pair(const GreenConst &gc, const float4 *subP,
+                                            const float4 *__restrict__ dtab, float xs, float zs,
+                                            int p, float q0, float2 (&Gr)[QB], float2 (&Gi)[QB]) {
+    const int nu = gc.nu;
+    const float t0 = TAB ? gc.tab_x0 * gc.tab_inv_dx : 0.0f, tmax = (float)gc.tab_n - 0.5f;
+#pragma unroll
+    for (int j = 0; j < QB; ++j) Gr[j] = Gi[j] = make_float2(0.f, 0.f);
+    for (int mu = 0; mu < nu; ++mu) {
+        const PairSetup2 P = pair_setup2(gc, subP + 3 * (p * nu + mu), xs, zs, q0);
+        float2 amp = P.amp0;
+        const float2 kt = TAB ? mul2(P.kap, dup2(gc.tab_inv_dx)) : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < QB; ++j) {
+            const float q = q0 + (float)j;
+            const float2 ph = mul2(dup2(6.283185307179586f), df_frac_mul2(dup2(q), P.u));
+            float2 sn, cs;
+            sincos_a(ph.x, sn.x, cs.x);
+            sincos_a(ph.y, sn.y, cs.y);
+            const float2 m = mul2(amp, sinc_f2<SINC>(mul2(dup2(q), P.xb)));
+            float dv[2][2];
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                PairSetup Pc;
+                Pc.kap = c ? P.kap.y : P.kap.x;
+                float2 d;
+                if (TAB) {
+                    const float tt = fmaf(q, c ? kt.y : kt.x, -t0);
+                    const float fl = floorf(fminf(fmaxf(tt, 0.0f), tmax));
+                    const int i = (int)fl;
+                    const float u = tt - fl;
+                    d = cubic_piece(__ldg(dtab + 2 * i), __ldg(dtab + 2 * i + 1), u);
+                    if (!(u >= 0.0f && u <= 1.0f)) d = delta_f<false>(gc, Pc, q);   // r < ~2 mm
+                } else {
+                    d = delta_f<false>(gc, Pc, q);
+                }
+                dv[c][0] = d.x;
+                dv[c][1] = d.y;
+            }
+            const float2 dre = make_float2(dv[0][0], dv[1][0]), dim = make_float2(dv[0][1], dv[1][1]);
+            const float2 er = mul2(cs, m), ei = mul2(sn, m);
+            Gr[j] = fma2(er, dre, fma2(neg2(ei), dim, Gr[j]));
+            Gi[j] = fma2(er, dim, fma2(ei, dre, Gi[j]));
+            amp = mul2(amp, P.mstep);
+        }
+    }
+}
+
 // TAB: delta/h at Y = 0 from the plan's table of cubic pieces (read-only cache; relative
 // error <= 2.3e-6), evaluated directly outside the table.
 template <int QB, bool HAS_Y, int SINC, bool TAB>
@@ -46,7 +98,7 @@ k_plain_mt(const GreenConst gc, const SubElem *__restrict__ sub_g, const float *
     float4 *sc = reinterpret_cast<float4 *>(smem_raw);              // [kMtSBMax] (x, y, z, R)
     float4 *subA = sc + kMtSBMax;                                   // [nu][N] xh, xl, zh, zl
     float4 *subB = subA + M;                                        // [nu][N] cpsi, spsi, l0, z0
-    float2 *cwt = reinterpret_cast<float2 *>(subB + M);             // [QB][T][Nr]
+    float2 *cwt = reinterpret_cast<float2 *>(subB + M + 3 * nu);    // [QB][T][Nr]
     float2 *rft = cwt + QB * T * Nr;                                // [QB][T][N]
     float2 *Gt = rft + QB * T * N;                                  // [QB][SB][Nr]
     float2 *RP = Gt + QB * SB * Nr;                                 // [QB][SB][T]
@@ -56,11 +108,20 @@ k_plain_mt(const GreenConst gc, const SubElem *__restrict__ sub_g, const float *
     const int64_t s_begin = (int64_t)chunk * chunk_len;
     const int64_t s_end = min(S, s_begin + chunk_len);
 
-    for (int i = tid; i < M; i += kMtThreads) {         // global [e][mu] -> shared [mu][e]
-        const float4 *rec = reinterpret_cast<const float4 *>(sub_g + i);
-        const int e = i / nu, mu = i - e * nu;
-        subA[mu * N + e] = rec[0];
-        subB[mu * N + e] = rec[1];
+    if (!HAS_Y) {       // element-pair records for mt_gen_pair (in place of the planes)
+        const int np = ((N + 1) >> 1) * nu;
+        for (int i = tid; i < np; i += kMtThreads) {
+            const int pp = i / nu, mu = i - pp * nu;
+            pair_records(sub_g[min(2 * pp, N - 1) * nu + mu], sub_g[min(2 * pp + 1, N - 1) * nu + mu],
+                         subA + 3 * i);
+        }
+    } else {
+        for (int i = tid; i < M; i += kMtThreads) {     // global [e][mu] -> shared [mu][e]
+            const float4 *rec = reinterpret_cast<const float4 *>(sub_g + i);
+            const int e = i / nu, mu = i - e * nu;
+            subA[mu * N + e] = rec[0];
+            subB[mu * N + e] = rec[1];
+        }
     }
     for (int i = tid; i < QB * T * N; i += kMtThreads) {
         const int j = i / (T * N), r = i - j * T * N, t = r / N, e = r - t * N, k = k0 + j;
@@ -86,8 +147,24 @@ k_plain_mt(const GreenConst gc, const SubElem *__restrict__ sub_g, const float *
         }
         __syncthreads();
 
-        // 1. Green's tile of the QB bins
-        for (int pr = tid; pr < SB * N; pr += kMtThreads) {
+        // 1. Green's tile of the QB bins (at Y = 0 two elements per item)
+        if (!HAS_Y) {
+            const int NP = (N + 1) >> 1;
+            for (int pr = tid; pr < SB * NP; pr += kMtThreads) {
+                const int s = pr / NP, pp = pr - s * NP;
+                const float4 ps = sc[s];
+                float2 Gr[QB], Gi[QB];
+                mt_gen_pair<QB, SINC, TAB>(gc, subA, dtab, ps.x, ps.z, pp, q0, Gr, Gi);
+                const int e0 = 2 * pp;
+#pragma unroll
+                for (int j = 0; j < QB; ++j) {
+                    float2 *o = Gt + (j * SB + s) * Nr + e0;
+                    o[0] = make_float2(Gr[j].x, Gi[j].x);
+                    if (e0 + 1 < N) o[1] = make_float2(Gr[j].y, Gi[j].y);
+                }
+            }
+        }
+        for (int pr = tid; pr < (HAS_Y ? SB * N : 0); pr += kMtThreads) {
             const int s = pr / N, e = pr - s * N;
             const float4 ps = sc[s];
             float2 G[QB];
@@ -219,7 +296,7 @@ k_plain_mt(const GreenConst gc, const SubElem *__restrict__ sub_g, const float *
 
 static size_t plain_mt_smem(const simus_plan *p, int T, int QB, int SB) {
     const size_t Nr = (size_t)p->N + 1;
-    return sizeof(float4) * kMtSBMax + sizeof(SubElem) * p->M
+    return sizeof(float4) * kMtSBMax + sizeof(SubElem) * p->M + 3 * sizeof(float4) * p->nu
          + sizeof(float2) * (size_t)QB * T * (Nr + p->N) + sizeof(float2) * (size_t)QB * SB * Nr
          + sizeof(float2) * (size_t)QB * SB * T;
 }
