@@ -62,6 +62,7 @@ def test_plan_bins_match_oracle(S, oracle):
     dict(y_spread=1.5e-3),                             # scatterers off the azimuth plane
     dict(elev_focus=float("inf")),
     dict(n_elements=24, n_scat=150, n_tx=7),           # one Green's tile for all transmits
+    dict(convex=True, n_elements=11, n_scat=60, n_tx=5),  # odd N: the last element pair half empty
     dict(n_elements=24, n_scat=70, n_tx=7, y_spread=1e-3),
     dict(n_elements=48, n_scat=40, n_tx=45),           # T N = 2160: smaller scatterer groups
     dict(n_elements=96, n_scat=12, n_tx=70),           # T N = 6720: per-transmit tiles
