@@ -42,7 +42,7 @@ extern "C" {
 #define SIMUS_ERR_CUDA (-2)        /* a CUDA runtime call or a launch failed         */
 #define SIMUS_ERR_OOM (-3)         /* device allocation of the workspace failed      */
 #define SIMUS_ERR_TIMEOUT (-4)     /* a bounded device wait gave up                  */
-#define SIMUS_ERR_UNSUPPORTED (-5) /* valid request this build does not implement    */
+#define SIMUS_ERR_UNSUPPORTED (-5) /* valid request the library does not implement   */
 
 /* Contraction path chosen at plan creation.
  *   PLAIN_F32 : Green's terms and every contraction in FP32 on the CUDA cores; with
