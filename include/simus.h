@@ -245,10 +245,15 @@ int simus_plan_get_timings(simus_plan *plan, float *ms);
  *                 default) or 1 (later bins of a pass wait in the tensor-memory stash)
  *   chunks        single simulations: scatterer chunks per bin tile (default: chosen by a
  *                 makespan model over the SMs)
+ *   depth_order   1: each simulation's scatterers are copied in order of their distance
+ *                 to the array into the workspace before the launch (default; the sum
+ *                 over scatterers is the same up to rounding, and tiles of similar depth
+ *                 take the same delta-table paths), 0: the caller's order
  * The project's autotuner (paper_2102_02738_gb300/autotune.py) times candidates through
  * these calls and caches the fastest per problem shape.
  * Returns SIMUS_ERR_ARG for a NULL plan or values out of range (max_bins > 64,
- * items_per_sm > 1024, chunks > 65536, pair > 2, delta_table > 1, tile_buffers > 2). */
+ * items_per_sm > 1024, chunks > 65536, pair > 2, delta_table > 1, tile_buffers > 2,
+ * depth_order > 1). */
 typedef struct simus_tuning {
     int32_t items_per_sm;
     int32_t max_bins;
@@ -256,7 +261,8 @@ typedef struct simus_tuning {
     int32_t delta_table;
     int32_t chunks;
     int32_t tile_buffers;
-    int32_t reserved[2];
+    int32_t depth_order;
+    int32_t reserved;
 } simus_tuning;
 int simus_plan_set_tuning(simus_plan *plan, const simus_tuning *tuning);
 int simus_plan_get_tuning(const simus_plan *plan, simus_tuning *tuning);

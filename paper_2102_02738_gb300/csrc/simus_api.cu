@@ -488,7 +488,7 @@ int simus_plan_set_profiling(simus_plan *plan, int32_t enable) {
 int simus_plan_set_tuning(simus_plan *plan, const simus_tuning *t) {
     if (!plan || !t) return fail(SIMUS_ERR_ARG, "plan and tuning must not be NULL");
     if (t->items_per_sm > 1024 || t->max_bins > 64 || t->chunks > 65536 || t->pair > 2 ||
-        t->delta_table > 1 || t->tile_buffers > 2)
+        t->delta_table > 1 || t->tile_buffers > 2 || t->depth_order > 1)
         return fail(SIMUS_ERR_ARG, "tuning value out of range");
     plan->items_per_sm = t->items_per_sm > 0 ? t->items_per_sm : 4;
     plan->max_bins = t->max_bins > 0 ? t->max_bins : 4;
@@ -496,6 +496,7 @@ int simus_plan_set_tuning(simus_plan *plan, const simus_tuning *t) {
     plan->delta_table = t->delta_table >= 0 ? t->delta_table : 1;
     plan->chunks = t->chunks > 0 ? t->chunks : 0;
     plan->tile_buffers = t->tile_buffers > 0 ? t->tile_buffers : 2;
+    plan->depth_order = t->depth_order >= 0 ? t->depth_order : 1;
     return SIMUS_OK;
 }
 
@@ -508,6 +509,7 @@ int simus_plan_get_tuning(const simus_plan *plan, simus_tuning *t) {
     t->delta_table = plan->delta_table;
     t->chunks = plan->chunks;
     t->tile_buffers = plan->tile_buffers;
+    t->depth_order = plan->depth_order;
     return SIMUS_OK;
 }
 
@@ -627,7 +629,7 @@ int tc_execute(simus_plan *owner, int n, simus_plan *const *plans, const simus_t
     // workspace
     const size_t units_b = align256(sizeof(TcUnit) * n_units);
     size_t off = units_b + 256;
-    std::vector<size_t> b1_off(n_units), part_off(nl), spec_off(nl);
+    std::vector<size_t> b1_off(n_units), part_off(nl), spec_off(nl), ord_off(nl);
     {
         int u = 0;
         for (int j = 0; j < nl; ++j)
@@ -641,6 +643,15 @@ int tc_execute(simus_plan *owner, int n, simus_plan *const *plans, const simus_t
             const simus_plan *p = plans[live[j]];
             spec_off[j] = off;
             if (!(specs && specs[live[j]])) off += align256(sizeof(float2) * (size_t)txs[live[j]].n_tx * p->N * p->nq);
+        }
+        // scatterers in distance order: x, y (when given), z, R and the sort's scratch
+        for (int j = 0; j < nl; ++j) {
+            const int i = live[j];
+            ord_off[j] = 0;
+            if (!plans[i]->depth_order || scs[i].n > (int64_t)INT32_MAX) continue;
+            ord_off[j] = off;
+            const size_t a = align256(sizeof(float) * (size_t)scs[i].n);
+            off += (scs[i].y ? 4 : 3) * a + align256(order_scratch_bytes(scs[i].n));
         }
     }
     void *ws;
@@ -687,6 +698,14 @@ int tc_execute(simus_plan *owner, int n, simus_plan *const *plans, const simus_t
             U.dtab = p->d_dtab;
             U.gc.tab_n = s.tab_n;
             U.x = scs[i].x; U.y = scs[i].y; U.z = scs[i].z; U.rc = scs[i].rc;
+            if (ord_off[j]) {   // the reordered copies (filled below, before the launch)
+                const size_t a = align256(sizeof(float) * (size_t)scs[i].n);
+                float *o = reinterpret_cast<float *>(base + ord_off[j]);
+                U.x = o;
+                U.z = reinterpret_cast<float *>(base + ord_off[j] + a);
+                U.rc = reinterpret_cast<float *>(base + ord_off[j] + 2 * a);
+                U.y = scs[i].y ? reinterpret_cast<float *>(base + ord_off[j] + 3 * a) : nullptr;
+            }
             U.delays = txs[i].delays; U.apod = txs[i].apod;
             U.S = scs[i].n; U.n_tiles = s.n_tiles;
             U.T = txs[i].n_tx; U.G = s.n_groups; U.TG = s.TG;
@@ -718,6 +737,17 @@ int tc_execute(simus_plan *owner, int n, simus_plan *const *plans, const simus_t
     }
     if ((rc = check_cuda(cudaMemsetAsync(counter, 0, sizeof(int), st), "memset counter"))) return rc;
     stage_begin(owner, 1, st);
+    for (int j = 0; j < nl; ++j) {
+        if (!ord_off[j]) continue;
+        const int i = live[j];
+        const size_t a = align256(sizeof(float) * (size_t)scs[i].n);
+        char *o = base + ord_off[j];
+        float *yo = scs[i].y ? reinterpret_cast<float *>(o + 3 * a) : nullptr;
+        int *scratch = reinterpret_cast<int *>(o + (scs[i].y ? 4 : 3) * a);
+        if ((rc = launch_order(&scs[i], (float)plans[i]->probe.radius, scratch, reinterpret_cast<float *>(o), yo,
+                               reinterpret_cast<float *>(o + a), reinterpret_cast<float *>(o + 2 * a), st)))
+            return rc;
+    }
     rc = launch_tc_units(hu, d_units, n_units, n_items, smem, owner->path == SIMUS_PATH_TC_BF16, has_y,
                          sinc_rank == 0 ? 1 : (sinc_rank == 1 ? 2 : 0), linear, owner->num_sms,
                          counter, owner->d_err, st);

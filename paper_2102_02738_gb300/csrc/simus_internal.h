@@ -70,6 +70,7 @@ struct simus_plan {
     int pair_mode = 2;
     int delta_table = 1;
     int tile_buffers = 2;
+    int depth_order = 1;              // tensor-core path: scatterers reordered by depth first
     int chunks = 0;
     bool profiling = false;
     bool stage_used[SIMUS_N_STAGES] = {};
@@ -163,6 +164,11 @@ struct TcShape {
 };
 // items_per_sm: target number of work items per SM over the whole launch (tuning).
 TcShape tc_shape(const simus_plan *p, int T, int64_t S, double work_share, int items_per_sm);
+// Scatterers of one simulation in distance-to-array order (k_order.cu): out arrays of
+// in->n floats (yo only when in->y), scratch of order_scratch_bytes(in->n).
+size_t order_scratch_bytes(int64_t S);
+int launch_order(const simus_scat *in, float R, int *scratch, float *xo, float *yo, float *zo,
+                 float *rco, cudaStream_t st);
 
 // One simulation, as the kernel reads it.
 struct TcUnit {

@@ -50,12 +50,15 @@ def rel_l2(a, b):
 def test_set_get_round_trip(S):
     w = ph.tiny(n_elements=16, n_scat=50, n_tx=3)
     plan = S.Plan(w.cfg, path="tc_f16")
-    default = dict(items_per_sm=4, max_bins=4, pair=2, delta_table=1, chunks=0, tile_buffers=2)
+    default = dict(items_per_sm=4, max_bins=4, pair=2, delta_table=1, chunks=0, tile_buffers=2,
+                   depth_order=1)
     assert plan.get_tuning() == default
-    plan.set_tuning(max_bins=6, pair=0, delta_table=0, chunks=3, items_per_sm=8, tile_buffers=1)
+    plan.set_tuning(max_bins=6, pair=0, delta_table=0, chunks=3, items_per_sm=8, tile_buffers=1,
+                    depth_order=0)
     assert plan.get_tuning() == dict(items_per_sm=8, max_bins=6, pair=0, delta_table=0, chunks=3,
-                                     tile_buffers=1)
-    plan.set_tuning(max_bins=-1, pair=-1, delta_table=-1, chunks=0, items_per_sm=-1, tile_buffers=0)
+                                     tile_buffers=1, depth_order=0)
+    plan.set_tuning(max_bins=-1, pair=-1, delta_table=-1, chunks=0, items_per_sm=-1, tile_buffers=0,
+                    depth_order=-1)
     assert plan.get_tuning() == default
     with pytest.raises(S.SimusError):
         plan.set_tuning(max_bins=65)
@@ -63,7 +66,30 @@ def test_set_get_round_trip(S):
         plan.set_tuning(pair=3)
     with pytest.raises(S.SimusError):
         plan.set_tuning(tile_buffers=3)
+    with pytest.raises(S.SimusError):
+        plan.set_tuning(depth_order=2)
     plan.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("convex", [False, True])
+def test_depth_order_matches_the_given_order_and_the_oracle(S, oracle, convex):
+    """Scatterers copied in distance-to-array order before the launch: the RF matches the
+    caller's order and the FP64 oracle within the tensor-core tolerance, and two calls in a
+    row give the same bits (the stable sort puts every scatterer at the same place)."""
+    w = ph.tiny(convex=convex, n_elements=24, n_scat=900, n_tx=5, nt=500)
+    ref = oracle.rf(w.cfg, w.delays, w.apod, w.x, w.y, w.z, w.rc)
+    plan = S.Plan(w.cfg, path="tc_f16")
+    args = [dev(v) for v in (w.delays, w.apod, w.x, w.y, w.z, w.rc)]
+    a = plan.rf(*args).cpu().numpy()
+    b = plan.rf(*args).cpu().numpy()
+    plan.set_tuning(depth_order=0)
+    c = plan.rf(*args).cpu().numpy()
+    plan.close()
+    assert np.array_equal(a, b)
+    assert rel_l2(a, ref) <= 2e-3
+    assert rel_l2(c, ref) <= 2e-3
+    assert rel_l2(a, c) <= 2e-3
 
 
 @pytest.mark.gpu
