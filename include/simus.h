@@ -249,11 +249,16 @@ int simus_plan_get_timings(simus_plan *plan, float *ms);
  *                 to the array into the workspace before the launch (default; the sum
  *                 over scatterers is the same up to rounding, and tiles of similar depth
  *                 take the same delta-table paths), 0: the caller's order
+ *   tensor_idft   1: the inverse DFT of Eq. 1 runs on the tensor cores as a product of
+ *                 split-BF16 operands (each value a BF16 leading part and a BF16
+ *                 remainder, three products, FP32 accumulation; about 2^-16 relative per
+ *                 term) where the plan holds its twiddles (plans whose blocked twiddles
+ *                 take at most 1 GiB; default), 0: on the CUDA cores in FP32
  * The project's autotuner (paper_2102_02738_gb300/autotune.py) times candidates through
  * these calls and caches the fastest per problem shape.
  * Returns SIMUS_ERR_ARG for a NULL plan or values out of range (max_bins > 64,
  * items_per_sm > 1024, chunks > 65536, pair > 2, delta_table > 1, tile_buffers > 2,
- * depth_order > 1). */
+ * depth_order > 1, tensor_idft > 1). */
 typedef struct simus_tuning {
     int32_t items_per_sm;
     int32_t max_bins;
@@ -262,7 +267,7 @@ typedef struct simus_tuning {
     int32_t chunks;
     int32_t tile_buffers;
     int32_t depth_order;
-    int32_t reserved;
+    int32_t tensor_idft;
 } simus_tuning;
 int simus_plan_set_tuning(simus_plan *plan, const simus_tuning *tuning);
 int simus_plan_get_tuning(const simus_plan *plan, simus_tuning *tuning);

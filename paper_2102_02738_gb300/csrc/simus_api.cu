@@ -418,6 +418,19 @@ int simus_plan_create(const simus_probe *probe, const simus_medium *medium, int3
     if (e == cudaSuccess) e = cudaMemset(p->d_err, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemcpy(p->d_sub, sub.data(), sizeof(SubElem) * p->M, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(p->d_H, H.data(), sizeof(float2) * p->nq, cudaMemcpyHostToDevice);
+    // tensor-core paths: the iDFT's twiddles, blocked for the tensor cores, when they take
+    // at most 1 GiB (larger problems keep the CUDA-core iDFT)
+    const size_t tw_b = idft_tc_twiddle_bytes(p->nt, p->nq);
+    int trc = SIMUS_OK;
+    if (e == cudaSuccess && p->path != SIMUS_PATH_PLAIN_F32 && tw_b <= ((size_t)1 << 30)) {
+        e = cudaMalloc(&p->d_idft_tw, tw_b);
+        if (e == cudaSuccess) trc = build_idft_tc_twiddles(p, p->d_idft_tw, nullptr);
+        if (e == cudaSuccess && !trc) e = cudaDeviceSynchronize();
+    }
+    if (trc) {
+        simus_plan_destroy(p);
+        return trc;
+    }
     if (e != cudaSuccess) {
         int r = check_cuda(e, "plan upload");
         cudaGetLastError();
@@ -442,6 +455,7 @@ void simus_plan_destroy(simus_plan *plan) {
     cudaFree(plan->d_H);
     cudaFree(plan->d_err);
     cudaFree(plan->d_dtab);
+    cudaFree(plan->d_idft_tw);
     cudaFree(plan->d_work);
     cudaSetDevice(cur);
     delete plan;
@@ -488,7 +502,7 @@ int simus_plan_set_profiling(simus_plan *plan, int32_t enable) {
 int simus_plan_set_tuning(simus_plan *plan, const simus_tuning *t) {
     if (!plan || !t) return fail(SIMUS_ERR_ARG, "plan and tuning must not be NULL");
     if (t->items_per_sm > 1024 || t->max_bins > 64 || t->chunks > 65536 || t->pair > 2 ||
-        t->delta_table > 1 || t->tile_buffers > 2 || t->depth_order > 1)
+        t->delta_table > 1 || t->tile_buffers > 2 || t->depth_order > 1 || t->tensor_idft > 1)
         return fail(SIMUS_ERR_ARG, "tuning value out of range");
     plan->items_per_sm = t->items_per_sm > 0 ? t->items_per_sm : 4;
     plan->max_bins = t->max_bins > 0 ? t->max_bins : 4;
@@ -497,6 +511,7 @@ int simus_plan_set_tuning(simus_plan *plan, const simus_tuning *t) {
     plan->chunks = t->chunks > 0 ? t->chunks : 0;
     plan->tile_buffers = t->tile_buffers > 0 ? t->tile_buffers : 2;
     plan->depth_order = t->depth_order >= 0 ? t->depth_order : 1;
+    plan->tensor_idft = t->tensor_idft >= 0 ? t->tensor_idft : 1;
     return SIMUS_OK;
 }
 
@@ -510,6 +525,7 @@ int simus_plan_get_tuning(const simus_plan *plan, simus_tuning *t) {
     t->chunks = plan->chunks;
     t->tile_buffers = plan->tile_buffers;
     t->depth_order = plan->depth_order;
+    t->tensor_idft = plan->tensor_idft;
     return SIMUS_OK;
 }
 
@@ -629,7 +645,7 @@ int tc_execute(simus_plan *owner, int n, simus_plan *const *plans, const simus_t
     // workspace
     const size_t units_b = align256(sizeof(TcUnit) * n_units);
     size_t off = units_b + 256;
-    std::vector<size_t> b1_off(n_units), part_off(nl), spec_off(nl), ord_off(nl);
+    std::vector<size_t> b1_off(n_units), part_off(nl), spec_off(nl), ord_off(nl), idft_off(nl);
     {
         int u = 0;
         for (int j = 0; j < nl; ++j)
@@ -643,6 +659,15 @@ int tc_execute(simus_plan *owner, int n, simus_plan *const *plans, const simus_t
             const simus_plan *p = plans[live[j]];
             spec_off[j] = off;
             if (!(specs && specs[live[j]])) off += align256(sizeof(float2) * (size_t)txs[live[j]].n_tx * p->N * p->nq);
+        }
+        // spectra blocked for the tensor-core iDFT
+        for (int j = 0; j < nl; ++j) {
+            const int i = live[j];
+            const simus_plan *p = plans[i];
+            idft_off[j] = 0;
+            if (!(rfs && rfs[i]) || !p->tensor_idft || !p->d_idft_tw) continue;
+            idft_off[j] = off;
+            off += align256(idft_tc_operand_bytes(txs[i].n_tx * p->N, p->nq));
         }
         // scatterers in distance order: x, y (when given), z, R and the sort's scratch
         for (int j = 0; j < nl; ++j) {
@@ -771,7 +796,9 @@ int tc_execute(simus_plan *owner, int n, simus_plan *const *plans, const simus_t
         if (!rfs[i]) continue;
         simus_plan *p = plans[i];
         float2 *spec = specs && specs[i] ? specs[i] : reinterpret_cast<float2 *>(base + spec_off[j]);
-        if ((rc = launch_idft(p, spec, txs[i].n_tx * p->N, rfs[i], st))) return rc;
+        rc = idft_off[j] ? launch_idft_tc(p, spec, txs[i].n_tx * p->N, rfs[i], base + idft_off[j], st)
+                         : launch_idft(p, spec, txs[i].n_tx * p->N, rfs[i], st);
+        if (rc) return rc;
     }
     stage_end(owner, 3, st);
     return SIMUS_OK;

@@ -59,6 +59,7 @@ struct simus_plan {
     float2 *d_H = nullptr;            // [nq] transfer S_P S_T at the kept bins
     int *d_err = nullptr;             // device-side error flag (bounded waits)
     float4 *d_dtab = nullptr;         // [2 gc.tab_n] delta/h cubic pieces (tensor-core path)
+    void *d_idft_tw = nullptr;        // blocked BF16 twiddles of the tensor-core iDFT (tensor-core paths)
     void *d_work = nullptr;           // workspace
     size_t work_bytes = 0;
     void *h_stage = nullptr;          // pinned host staging of work descriptors
@@ -71,6 +72,7 @@ struct simus_plan {
     int delta_table = 1;
     int tile_buffers = 2;
     int depth_order = 1;              // tensor-core path: scatterers reordered by depth first
+    int tensor_idft = 1;              // tensor-core path: iDFT on the tensor cores (if d_idft_tw)
     int chunks = 0;
     bool profiling = false;
     bool stage_used[SIMUS_N_STAGES] = {};
@@ -218,5 +220,13 @@ int launch_reduce_spectrum(const simus_plan *p, const float2 *part, int n_chunks
 
 // rf[c][j] = Re sum_k spec[c][k] e^{-2 pi i (q_lo + k) j / Nt}.
 int launch_idft(const simus_plan *p, const float2 *spec, int n_chan, float *rf, cudaStream_t st);
+// The same on the tensor cores (split-BF16 operands, FP32 accumulation): spectra blocked
+// into blocks_ws (idft_tc_operand_bytes), then one GEMM with p->d_idft_tw, which
+// build_idft_tc_twiddles fills (idft_tc_twiddle_bytes).
+size_t idft_tc_twiddle_bytes(int nt, int nq);
+size_t idft_tc_operand_bytes(int n_chan, int nq);
+int build_idft_tc_twiddles(const simus_plan *p, void *tw, cudaStream_t st);
+int launch_idft_tc(const simus_plan *p, const float2 *spec, int n_chan, float *rf, void *blocks_ws,
+                   cudaStream_t st);
 
 }  // namespace simus

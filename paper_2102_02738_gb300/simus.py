@@ -63,11 +63,11 @@ class PlanInfo(C.Structure):
 class Tuning(C.Structure):
     _fields_ = [("items_per_sm", C.c_int32), ("max_bins", C.c_int32), ("pair", C.c_int32),
                 ("delta_table", C.c_int32), ("chunks", C.c_int32), ("tile_buffers", C.c_int32),
-                ("depth_order", C.c_int32), ("reserved", C.c_int32)]
+                ("depth_order", C.c_int32), ("tensor_idft", C.c_int32)]
 
 
 TUNING_FIELDS = ("items_per_sm", "max_bins", "pair", "delta_table", "chunks", "tile_buffers",
-                 "depth_order")
+                 "depth_order", "tensor_idft")
 
 
 def _load():

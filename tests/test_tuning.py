@@ -51,14 +51,14 @@ def test_set_get_round_trip(S):
     w = ph.tiny(n_elements=16, n_scat=50, n_tx=3)
     plan = S.Plan(w.cfg, path="tc_f16")
     default = dict(items_per_sm=4, max_bins=4, pair=2, delta_table=1, chunks=0, tile_buffers=2,
-                   depth_order=1)
+                   depth_order=1, tensor_idft=1)
     assert plan.get_tuning() == default
     plan.set_tuning(max_bins=6, pair=0, delta_table=0, chunks=3, items_per_sm=8, tile_buffers=1,
-                    depth_order=0)
+                    depth_order=0, tensor_idft=0)
     assert plan.get_tuning() == dict(items_per_sm=8, max_bins=6, pair=0, delta_table=0, chunks=3,
-                                     tile_buffers=1, depth_order=0)
+                                     tile_buffers=1, depth_order=0, tensor_idft=0)
     plan.set_tuning(max_bins=-1, pair=-1, delta_table=-1, chunks=0, items_per_sm=-1, tile_buffers=0,
-                    depth_order=-1)
+                    depth_order=-1, tensor_idft=-1)
     assert plan.get_tuning() == default
     with pytest.raises(S.SimusError):
         plan.set_tuning(max_bins=65)
@@ -68,6 +68,8 @@ def test_set_get_round_trip(S):
         plan.set_tuning(tile_buffers=3)
     with pytest.raises(S.SimusError):
         plan.set_tuning(depth_order=2)
+    with pytest.raises(S.SimusError):
+        plan.set_tuning(tensor_idft=2)
     plan.close()
 
 
@@ -90,6 +92,36 @@ def test_depth_order_matches_the_given_order_and_the_oracle(S, oracle, convex):
     assert rel_l2(a, ref) <= 2e-3
     assert rel_l2(c, ref) <= 2e-3
     assert rel_l2(a, c) <= 2e-3
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("case", [
+    dict(n_elements=24, n_tx=5, nt=500, path="tc_f16"),       # 120 channels: one ragged tile
+    dict(n_elements=64, n_tx=5, nt=700, path="tc_bf16"),      # 320 channels: two tiles, ragged
+    dict(n_elements=16, n_tx=3, nt=96, path="tc_f16"),        # fewer K chunks than stages
+    dict(n_elements=48, n_tx=11, nt=1031, path="tc_f16"),     # 528 channels, nt ragged by 7
+])
+def test_tensor_idft_matches_the_cuda_core_idft(S, oracle, case):
+    """The inverse DFT on the tensor cores (split-BF16 twiddles and spectra, FP32
+    accumulation, about 2^-16 relative per term) against the FP32 CUDA-core iDFT of the
+    same spectrum, over channel and sample counts that leave ragged tiles, and both
+    against the FP64 oracle."""
+    w = ph.tiny(convex=True, n_elements=case["n_elements"], n_scat=300, n_tx=case["n_tx"],
+                nt=case["nt"])
+    ref = oracle.rf(w.cfg, w.delays, w.apod, w.x, w.y, w.z, w.rc)
+    plan = S.Plan(w.cfg, path=case["path"])
+    args = [dev(v) for v in (w.delays, w.apod, w.x, w.y, w.z, w.rc)]
+    a = plan.rf(*args).cpu().numpy()
+    b = plan.rf(*args).cpu().numpy()
+    plan.set_tuning(tensor_idft=0)
+    c = plan.rf(*args).cpu().numpy()
+    assert S.lib.simus_plan_check(plan.handle) == 0
+    plan.close()
+    assert a.shape == c.shape == ref.shape
+    assert np.array_equal(a, b)
+    assert rel_l2(a, c) <= 1e-4
+    assert float(np.abs(a - c).max()) <= 1e-4 * float(np.abs(c).max())
+    assert rel_l2(a, ref) <= TOL_TC
 
 
 @pytest.mark.gpu
