@@ -660,15 +660,18 @@ int tc_execute(simus_plan *owner, int n, simus_plan *const *plans, const simus_t
             spec_off[j] = off;
             if (!(specs && specs[live[j]])) off += align256(sizeof(float2) * (size_t)txs[live[j]].n_tx * p->N * p->nq);
         }
-        // spectra blocked for the tensor-core iDFT
+        // spectra blocked for the tensor-core iDFT: one region for the largest, as the
+        // simulations' iDFTs run one after another on the stream
+        size_t idft_b = 0;
         for (int j = 0; j < nl; ++j) {
             const int i = live[j];
             const simus_plan *p = plans[i];
             idft_off[j] = 0;
             if (!(rfs && rfs[i]) || !p->tensor_idft || !p->d_idft_tw) continue;
             idft_off[j] = off;
-            off += align256(idft_tc_operand_bytes(txs[i].n_tx * p->N, p->nq));
+            idft_b = std::max(idft_b, align256(idft_tc_operand_bytes(txs[i].n_tx * p->N, p->nq)));
         }
+        off += idft_b;
         // scatterers in distance order: x, y (when given), z, R and the sort's scratch
         for (int j = 0; j < nl; ++j) {
             const int i = live[j];
