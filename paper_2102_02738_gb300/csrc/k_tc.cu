@@ -55,37 +55,41 @@ size_t unit_smem(int Np, int nN, int nbuf, int M, int tab_n, bool split) {
 // operand of the transmit GEMM for transmits g TG .. g TG + TG - 1 (image [k][g]),
 //   row 2t: (Re C, -Im C), row 2t+1: (Im C, Re C), C = W exp(i 2 pi frac(q df dtau)).
 // BF16 images are split: the BF16 leading parts, then the BF16 remainders C - hi.
+// One thread per complex weight (transmit slot, element) of an image, writing its four
+// entries; blockIdx.y strides over the images.
+template <bool BF16>
+__device__ __forceinline__ void put_weight(uint16_t *im, int per_img, uint32_t o, float v) {
+    im[o] = h16<BF16>(v);
+    if (BF16) im[o + per_img] = h16<true>(v - __bfloat162float(__float2bfloat16_rn(v)));
+}
 template <bool BF16>
 __global__ void k_tc_weights(int T, int G, int TG, int N, int Np, int nN, int nq, int q_lo,
                              double df, const float *__restrict__ delays,
                              const float *__restrict__ apod, uint16_t *__restrict__ img) {
-    const int K = 2 * Np;
-    const int64_t per_img = (int64_t)nN * K;
+    const int K = 2 * Np, per_img = nN * K, n_w = (nN / 2) * Np;
     constexpr int kOps = BF16 ? 2 : 1;
-    const int64_t total = per_img * G * nq;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t kg = i / per_img;
-        int k = (int)(kg / G), g = (int)(kg % G);
-        int r = (int)(i % per_img);
-        int n = r / K, kk = r % K;
-        int tl = n >> 1;
-        int t = g * TG + tl;
-        int e = kk < Np ? kk : kk - Np;
-        float v = 0.f;
-        if (tl < TG && t < T && e < N) {
-            double ph = (double)(q_lo + k) * ((double)delays[t * N + e] * df);
-            ph -= rint(ph);
-            float s, c;
-            sincospif((float)(2.0 * ph), &s, &c);
-            float w = apod[t * N + e];
-            float cr = w * c, ci = w * s;
-            bool first_half = kk < Np;
-            v = (n & 1) ? (first_half ? ci : cr) : (first_half ? cr : -ci);
+    for (int kg = blockIdx.y; kg < nq * G; kg += gridDim.y) {
+        const int k = kg / G, g = kg - k * G;
+        uint16_t *im = img + (size_t)kg * kOps * per_img;
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_w; i += gridDim.x * blockDim.x) {
+            const int tl = i / Np, e = i - tl * Np;
+            const int t = g * TG + tl;
+            float cr = 0.f, ci = 0.f;
+            if (tl < TG && t < T && e < N) {
+                double ph = (double)(q_lo + k) * ((double)delays[t * N + e] * df);
+                ph -= rint(ph);
+                float s, c;
+                sincospif((float)(2.0 * ph), &s, &c);
+                const float w = apod[t * N + e];
+                cr = w * c;
+                ci = w * s;
+            }
+            const int n = 2 * tl;
+            put_weight<BF16>(im, per_img, tc::kmajor_offset(n, e, K) / 2, cr);
+            put_weight<BF16>(im, per_img, tc::kmajor_offset(n, Np + e, K) / 2, -ci);
+            put_weight<BF16>(im, per_img, tc::kmajor_offset(n + 1, e, K) / 2, ci);
+            put_weight<BF16>(im, per_img, tc::kmajor_offset(n + 1, Np + e, K) / 2, cr);
         }
-        const size_t o = (size_t)kg * kOps * per_img + tc::kmajor_offset(n, kk, K) / 2;
-        img[o] = h16<BF16>(v);
-        if (BF16) img[o + per_img] = h16<true>(v - __bfloat162float(__float2bfloat16_rn(v)));
     }
 }
 
@@ -203,8 +207,8 @@ int launch_tc_units(const TcUnit *h_units, const TcUnit *d_units, int n_units, i
                     int *counter, int *err, cudaStream_t st) {
     for (int u = 0; u < n_units; ++u) {
         const TcUnit &U = h_units[u];
-        int64_t total = (int64_t)U.gc.nq * U.G * U.nN * 2 * U.Np;
-        int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)num_sms * 16);
+        const int n_w = (U.nN / 2) * U.Np;
+        const dim3 blocks((n_w + 255) / 256, (unsigned)std::min<int64_t>((int64_t)U.gc.nq * U.G, 65535));
         if (bf16)
             k_tc_weights<true><<<blocks, 256, 0, st>>>(U.T, U.G, U.TG, U.gc.N, U.Np, U.nN, U.gc.nq,
                                                        U.gc.q_lo, U.gc.df, U.delays, U.apod, U.b1img);

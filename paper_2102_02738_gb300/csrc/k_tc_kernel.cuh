@@ -208,8 +208,9 @@ __device__ __forceinline__ float2 sinc_short2(float2 x) {
 // coordinates, one Newton step on r, exact double-float phase rate), phase seed and
 // phasor recurrence, sinc fit and delta table, each FP32 operation of both chains one
 // f32x2 instruction; the SFU operations, the table pieces (rows differ per chain) and the
-// range checks stay per chain.  sub: paired records (paired_sub).
-template <int NB, bool TAB, int SINC, bool LINEAR>
+// range checks stay per chain.  sub: paired records (paired_sub).  QUAD: the table holds
+// quadratic pieces (the FP16 kernels), else cubic ones (split BF16).
+template <int NB, bool TAB, int SINC, bool LINEAR, bool QUAD>
 __device__ __forceinline__ void gen_two2(const GreenConst &gc, const float4 *sub,
                                          const float4 *tabs, const float4 &ps, int e0, float qA,
                                          float2 (&ore)[NB], float2 (&oim)[NB]) {
@@ -273,7 +274,15 @@ __device__ __forceinline__ void gen_two2(const GreenConst &gc, const float4 *sub
         float4 lo[2], hi[2];
         if (TAB) {
 #pragma unroll
-            for (int c = 0; c < 2; ++c) { lo[c] = tabs[2 * ti[c]]; hi[c] = tabs[2 * ti[c] + 1]; }
+            for (int c = 0; c < 2; ++c) {
+                lo[c] = tabs[2 * ti[c]];
+                if (QUAD) {   // c2 only
+                    const float2 h = reinterpret_cast<const float2 *>(tabs)[2 * (2 * ti[c] + 1)];
+                    hi[c] = make_float4(h.x, h.y, 0.f, 0.f);
+                } else {
+                    hi[c] = tabs[2 * ti[c] + 1];
+                }
+            }
         }
         // phase seed at the first bin (exact reduction of q u), then the phasor step
         float2 zr, zi, wr = make_float2(0.f, 0.f), wi = make_float2(0.f, 0.f);
@@ -314,8 +323,8 @@ __device__ __forceinline__ void gen_two2(const GreenConst &gc, const float4 *sub
 #pragma unroll
             for (int b = 0; b < NB; ++b) {
                 const float2 ub = fma2(dup2((float)b), kt, u);
-                d[0][b] = cubic_piece(lo[0], hi[0], ub.x);
-                d[1][b] = cubic_piece(lo[1], hi[1], ub.y);
+                d[0][b] = QUAD ? quad_piece(lo[0], make_float2(hi[0].x, hi[0].y), ub.x) : cubic_piece(lo[0], hi[0], ub.x);
+                d[1][b] = QUAD ? quad_piece(lo[1], make_float2(hi[1].x, hi[1].y), ub.y) : cubic_piece(lo[1], hi[1], ub.y);
             }
         }
         if (TAB && NB > 1 && far) {
@@ -332,7 +341,8 @@ __device__ __forceinline__ void gen_two2(const GreenConst &gc, const float4 *sub
                         const float fl = floorf(fminf(fmaxf(tb, 0.0f), tmax));
                         const int i = (int)fl;
                         const float v = tb - fl;
-                        d[c][b] = cubic_piece(tabs[2 * i], tabs[2 * i + 1], v);
+                        d[c][b] = QUAD ? quad_piece(tabs[2 * i], reinterpret_cast<const float2 *>(tabs)[2 * (2 * i + 1)], v)
+                                       : cubic_piece(tabs[2 * i], tabs[2 * i + 1], v);
                         ok = ok && v >= 0.0f && v <= 1.0f;
                     }
                 }
@@ -384,7 +394,7 @@ __device__ __forceinline__ void gen_tiles(const GreenConst &gc, const float4 *su
                 gen_two<NB, TAB, HAS_Y, SINC, LINEAR>(gc, sub, tabs, ps, eg * 8 + 2 * jp, qA, o);
             } else {
                 float2 ore[NB], oim[NB];
-                gen_two2<NB, TAB, SINC, LINEAR>(gc, sub, tabs, ps, eg * 8 + 2 * jp, qA, ore, oim);
+                gen_two2<NB, TAB, SINC, LINEAR, !SPLIT>(gc, sub, tabs, ps, eg * 8 + 2 * jp, qA, ore, oim);
 #pragma unroll
                 for (int b = 0; b < NB; ++b) {
                     o[0][b][0] = ore[b].x; o[1][b][0] = ore[b].y;

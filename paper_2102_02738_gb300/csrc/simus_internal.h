@@ -58,7 +58,8 @@ struct simus_plan {
     simus::SubElem *d_sub = nullptr;  // [M]
     float2 *d_H = nullptr;            // [nq] transfer S_P S_T at the kept bins
     int *d_err = nullptr;             // device-side error flag (bounded waits)
-    float4 *d_dtab = nullptr;         // [2 gc.tab_n] delta/h cubic pieces (tensor-core path)
+    float4 *d_dtab = nullptr;         // [2 gc.tab_n] delta/h cubic pieces
+    float4 *d_dtab_q = nullptr;       // [2 gc.tab_n] the same as quadratic pieces (FP16 tensor-core kernels)
     void *d_idft_tw = nullptr;        // blocked BF16 twiddles of the tensor-core iDFT (tensor-core paths)
     void *d_work = nullptr;           // workspace
     size_t work_bytes = 0;
@@ -93,8 +94,10 @@ void plan_fill_tables(const simus_plan *p, SubElem *sub, float2 *H);
 // Cubic Hermite table of delta/h over the x = h^2 Im(alpha_g - B_g/h^2) reachable by the
 // plan's bins for scatterers at least 2 mm from a sub-element (spacing 0.5, relative error
 // <= 2.3e-6), as power-basis pieces (two float4 per interval); sets gc.tab_x0, tab_inv_dx,
-// tab_n = intervals (0 if it would exceed 2048).
-void plan_delta_table(simus_plan *p, std::vector<float4> &tab);
+// tab_n = intervals (0 if it would exceed 2048); tab_q: the quadratic through each interval's
+// ends and midpoint in the same layout (c3 = 0; relative error <= 1.9e-5), for the FP16
+// tensor-core kernels.
+void plan_delta_table(simus_plan *p, std::vector<float4> &tab, std::vector<float4> &tab_q);
 GreenConst green_const(const simus_probe &pr, const simus_medium &md, int N, int nu, double df,
                        double q_max);
 
@@ -176,7 +179,8 @@ int launch_order(const simus_scat *in, float R, int *scratch, float *xo, float *
 struct TcUnit {
     GreenConst gc;
     const SubElem *sub;
-    const float4 *dtab;           // delta/h cubic pieces [2 gc.tab_n] (gc.tab_n = 0: direct)
+    const float4 *dtab;           // delta/h pieces [2 gc.tab_n]: quadratic for FP16, cubic for split
+                                  // BF16 (gc.tab_n = 0: direct)
     const float *x, *y, *z, *rc;
     const float *delays, *apod;   // of the whole simulation, [T][N]
     int64_t S, n_tiles;
