@@ -39,12 +39,12 @@ from paper_2102_02738_gb300 import phantoms as ph  # noqa: E402
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the dominant kernel, from
 # the ncu capture summarised in profiles/ (per launch; absent where the kernel changed
 # after the capture or none was taken)
-NCU_TRAFFIC = {("diverging-convex-128", "tc_f16", 100000): 48.552704e6 + 222.424576e6,
+NCU_TRAFFIC = {("diverging-convex-128", "tc_f16", 100000): 50.636544e6 + 223.560448e6,
                ("planewave-linear-128", "plain", 20003): 1.477632e6 + 0.005120e6}
 # thread instructions per unique Green's term of the dominant kernel, from the same
 # workloads' full captures (smsp__inst_executed.sum x 32 / unique terms); used for the
 # issue-slot fraction
-INST_PER_TERM = {("diverging-convex-128", "tc_f16", 100000): 3.2488236458e10 * 32 / (864 * 100000 * 256),
+INST_PER_TERM = {("diverging-convex-128", "tc_f16", 100000): 3.1100394648e10 * 32 / (864 * 100000 * 256),
                  ("planewave-linear-128", "plain", 20003): 1.633e10 * 32 / (763 * 20003 * 384)}
 # k_pfield on the 201 x 201 L11-5v grid (15 frequency chunks): DRAM read + write per launch
 PFIELD_TRAFFIC = 1.250048e6
