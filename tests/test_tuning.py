@@ -125,6 +125,28 @@ def test_tensor_idft_matches_the_cuda_core_idft(S, oracle, case):
 
 
 @pytest.mark.gpu
+def test_tensor_idft_launches_its_own_kernels(S):
+    """With tensor_idft = 1 the iDFT stage is two launches of this library (the spectra
+    blocked into split BF16, then the tcgen05 product), with 0 one (the CUDA-core iDFT);
+    nothing else in the call changes."""
+    w = ph.tiny(convex=True, n_elements=16, n_scat=100, n_tx=3, nt=300)
+    plan = S.Plan(w.cfg, path="tc_f16")
+    args = [dev(v) for v in (w.delays, w.apod, w.x, w.y, w.z, w.rc)]
+    plan.rf(*args)                                   # warm-up: workspace, staging
+    counts = []
+    for t in (1, 0):
+        plan.set_tuning(tensor_idft=t)
+        torch.cuda.synchronize()
+        n0 = S.simus_kernel_launches()
+        plan.rf(*args)
+        torch.cuda.synchronize()
+        counts.append(S.simus_kernel_launches() - n0)
+    assert S.lib.simus_plan_check(plan.handle) == 0
+    plan.close()
+    assert counts[0] == counts[1] + 1
+
+
+@pytest.mark.gpu
 @pytest.mark.parametrize("tun", [dict(max_bins=2, pair=1, delta_table=1),
                                  dict(max_bins=6, pair=2, delta_table=1),
                                  dict(max_bins=3, pair=2, delta_table=0, chunks=3),
