@@ -136,7 +136,11 @@ typedef struct simus_plan simus_plan;
  * kept frequency bins -- the contiguous range of 1 <= q < Nt/2 on which the transfer
  * magnitude |S_P S_T| (Eq. 25-28, Eq. 34) is at least 1e-5 of its maximum -- and the
  * transfer values H_q = S_P(w_q) S_T(w_q).  n_samples is the RF length Nt (>= 8).
- * Host-only apart from uploading the tables to the current device.
+ * Host-only apart from uploading the tables to the current device; plans of the
+ * tensor-core paths also build the inverse DFT's twiddles on that device (one kernel,
+ * then a device synchronisation): ceil(Nt/128) * ceil(2 n_bins/32) * 16 KiB of device
+ * memory held by the plan (none where that would exceed 1 GiB: their iDFT then runs on
+ * the CUDA cores).  All of it is freed by simus_plan_destroy.
  * Returns SIMUS_ERR_ARG on invalid parameters, SIMUS_ERR_CUDA/OOM on upload failure. */
 int simus_plan_create(const simus_probe *probe, const simus_medium *medium,
                       int32_t n_samples, int32_t path, simus_plan **out);
