@@ -150,10 +150,22 @@ __device__ __forceinline__ void gen_two(const GreenConst &gc, const float4 *sub,
                 }
         }
         if (!ok) {   // outside the table (within ~2 mm of the sub-element): Eq. 16 directly
+            if (HAS_Y) {   // both chains' Eq. 14 as packed pairs
+                const float2 kap2 = make_float2(P[0].kap, P[1].kap), y2 = make_float2(P[0].y, P[1].y);
+                const float2 ir2 = make_float2(P[0].inv_r, P[1].inv_r);
 #pragma unroll
-            for (int c = 0; c < 2; ++c)
+                for (int b = 0; b < NB; ++b) {
+                    float2 dr, di;
+                    delta_y2(gc, kap2, y2, ir2, qA + (float)b, dr, di);
+                    d[0][b] = make_float2(dr.x, di.x);
+                    d[1][b] = make_float2(dr.y, di.y);
+                }
+            } else {
 #pragma unroll
-                for (int b = 0; b < NB; ++b) d[c][b] = delta_f<HAS_Y>(gc, P[c], qA + (float)b);
+                for (int c = 0; c < 2; ++c)
+#pragma unroll
+                    for (int b = 0; b < NB; ++b) d[c][b] = delta_f<HAS_Y>(gc, P[c], qA + (float)b);
+            }
         }
 #pragma unroll
         for (int b = 0; b < NB; ++b)

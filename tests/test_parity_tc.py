@@ -52,6 +52,8 @@ TINY = [
     dict(n_elements=13, n_sub=3, n_scat=150, n_tx=3),        # N not a multiple of 8
     dict(convex=True, n_elements=24, n_scat=200, n_tx=9),
     dict(y_spread=1e-3, n_scat=130),
+    dict(convex=True, n_elements=24, n_scat=300, n_tx=5, y_spread=2e-3),   # Y != 0, convex
+    dict(n_elements=13, n_sub=3, n_scat=150, n_tx=3, y_spread=1.5e-3),     # Y != 0, odd N
     # wide arrays: 96-112 KB tiles leave room for one shared-memory tile buffer, so the
     # later bins of a pass wait in tensor-memory stash slots
     dict(n_elements=176, n_sub=1, n_scat=140, n_tx=3),      # two buffers, receive in halves
