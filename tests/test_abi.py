@@ -53,7 +53,8 @@ int main(void) {
          sizeof(simus_scat), sizeof(simus_plan_info));
   printf("%zu %zu %zu %zu\n", offsetof(simus_probe, pitch), offsetof(simus_medium, pulse_cycles),
          offsetof(simus_tx, apod), offsetof(simus_plan_info, df));
-  printf("%zu %zu\n", sizeof(simus_tuning), offsetof(simus_tuning, chunks));
+  printf("%zu %zu %zu %zu\n", sizeof(simus_tuning), offsetof(simus_tuning, chunks),
+         offsetof(simus_tuning, depth_order), offsetof(simus_tuning, tensor_idft));
   return 0; }
 ''')
     exe = tmp_path / "layout"
@@ -61,7 +62,8 @@ int main(void) {
     out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
     got = [C.sizeof(S.Probe), C.sizeof(S.Medium), C.sizeof(S.Tx), C.sizeof(S.Scat),
            C.sizeof(S.PlanInfo), S.Probe.pitch.offset, S.Medium.pulse_cycles.offset,
-           S.Tx.apod.offset, S.PlanInfo.df.offset, C.sizeof(S.Tuning), S.Tuning.chunks.offset]
+           S.Tx.apod.offset, S.PlanInfo.df.offset, C.sizeof(S.Tuning), S.Tuning.chunks.offset,
+           S.Tuning.depth_order.offset, S.Tuning.tensor_idft.offset]
     assert [int(v) for v in out] == got
 
 
