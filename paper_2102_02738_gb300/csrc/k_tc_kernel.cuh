@@ -41,144 +41,6 @@ __device__ __forceinline__ void bf16_split2(float a, float b, uint32_t &hi, uint
 }
 
 
-// Sub-element sums (Eq. 33) of the Green's terms of elements e0 and e0 + 1 for one
-// scatterer at the NB consecutive bins qA, qA + 1, ...: two independent evaluation chains
-// side by side, so that each warp has twice the instruction-level parallelism, and one
-// geometry setup per (scatterer, sub-element) for all NB bins.  An element past N is
-// evaluated on element N - 1 with zero amplitude (no branch).  With the delta table, bin
-// qA picks the cubic piece and the later bins reuse it: bin qA + b moves u by b kap/dx,
-// small except within a few mm of the sub-element; up to half an interval outside the
-// piece the cubic is extrapolated (error <= 9 times the in-piece error), beyond that the
-// bin takes its own piece, and outside the table delta is evaluated directly.
-// o[c][b] = (Re, Im) of element e0 + c at bin qA + b.
-template <int NB, bool TAB, bool HAS_Y, int SINC, bool LINEAR>
-__device__ __forceinline__ void gen_two(const GreenConst &gc, const float4 *sub,
-                                        const float4 *tabs, const float4 &ps, int e0, float qA,
-                                        float (&o)[2][NB][2]) {
-    const int N = gc.N, nu = gc.nu;
-    const float w0 = e0 < N ? 1.0f : 0.0f, w1 = e0 + 1 < N ? 1.0f : 0.0f;
-    const int b0 = min(e0, N - 1) * nu, b1 = min(e0 + 1, N - 1) * nu;
-    const float t0 = gc.tab_x0 * gc.tab_inv_dx, tmax = (float)gc.tab_n - 0.5f;
-#pragma unroll
-    for (int c = 0; c < 2; ++c)
-#pragma unroll
-        for (int b = 0; b < NB; ++b) o[c][b][0] = o[c][b][1] = 0.0f;
-    for (int mu = 0; mu < nu; ++mu) {
-        PairSetup P[2];
-        P[0] = pair_setup_f32<HAS_Y, LINEAR>(gc, sub[b0 + mu], ps.x, ps.y, ps.z, qA);
-        P[1] = pair_setup_f32<HAS_Y, LINEAR>(gc, sub[b1 + mu], ps.x, ps.y, ps.z, qA);
-        P[0].amp0 *= w0;
-        P[1].amp0 *= w1;
-        float kt[2] = {0.0f, 0.0f}, u[2] = {0.0f, 0.0f};
-        int ti[2] = {0, 0};
-        bool ok = TAB, far = false;
-        float tq[2] = {0.0f, 0.0f};
-        if (TAB) {
-#pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                kt[c] = P[c].kap * gc.tab_inv_dx;
-                tq[c] = fmaf(qA, kt[c], -t0);
-                const float fl = floorf(fminf(fmaxf(tq[c], 0.0f), tmax));
-                ti[c] = (int)fl;
-                u[c] = tq[c] - fl;
-                const float ue = fmaf((float)(NB - 1), kt[c], u[c]);   // the last bin's u
-                ok = ok && u[c] >= 0.0f && u[c] <= 1.0f;
-                far = far || !(ue >= -0.5f && ue <= 1.5f);
-            }
-        }
-        float4 lo[2], hi[2];            // the pieces (index clamped: always a valid load)
-        if (TAB) {
-#pragma unroll
-            for (int c = 0; c < 2; ++c) { lo[c] = tabs[2 * ti[c]]; hi[c] = tabs[2 * ti[c] + 1]; }
-        }
-        // phase, absorption and sinc directivity of every bin (common to both delta forms):
-        // z = amp0 exp(i 2 pi frac(qA u)) at the first bin, then z <- z w with
-        // w = mstep exp(i 2 pi frac(u)) per further bin (phase and absorption of one bin)
-        float er[2][NB], ei[2][NB];
-        float zr[2], zi[2], wr[2] = {0.0f, 0.0f}, wi[2] = {0.0f, 0.0f};
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            float sn, cs;
-            sincos_a(6.283185307179586f * df_frac_mul(qA, P[c].u), sn, cs);
-            zr[c] = P[c].amp0 * cs;
-            zi[c] = P[c].amp0 * sn;
-            if (NB > 1) {
-                const float fu = (P[c].u.h - rintf(P[c].u.h)) + P[c].u.l;
-                sincos_a(6.283185307179586f * fu, sn, cs);
-                wr[c] = P[c].mstep * cs;
-                wi[c] = P[c].mstep * sn;
-            }
-        }
-#pragma unroll
-        for (int b = 0; b < NB; ++b) {
-            const float q = qA + (float)b;
-#pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                const float m = sinc_short<SINC>(q * P[c].xb);
-                er[c][b] = zr[c] * m;
-                ei[c][b] = zi[c] * m;
-                if (b + 1 < NB) {
-                    const float nzr = fmaf(zr[c], wr[c], -zi[c] * wi[c]);
-                    zi[c] = fmaf(zr[c], wi[c], zi[c] * wr[c]);
-                    zr[c] = nzr;
-                }
-            }
-        }
-        float2 d[2][NB];
-        if (TAB) {
-#pragma unroll
-            for (int c = 0; c < 2; ++c)
-#pragma unroll
-                for (int b = 0; b < NB; ++b) d[c][b] = cubic_piece(lo[c], hi[c], fmaf((float)b, kt[c], u[c]));
-        }
-        if (TAB && NB > 1 && far) {
-            // a later bin moved more than half an interval past its piece (scatterers a few
-            // mm from the sub-element): it takes its own piece
-#pragma unroll
-            for (int c = 0; c < 2; ++c)
-#pragma unroll
-                for (int b = 1; b < NB; ++b) {
-                    const float ub = fmaf((float)b, kt[c], u[c]);
-                    if (!(ub >= -0.5f && ub <= 1.5f)) {
-                        const float tb = fmaf((float)b, kt[c], tq[c]);
-                        const float fl = floorf(fminf(fmaxf(tb, 0.0f), tmax));
-                        const int i = (int)fl;
-                        const float v = tb - fl;
-                        d[c][b] = cubic_piece(tabs[2 * i], tabs[2 * i + 1], v);
-                        ok = ok && v >= 0.0f && v <= 1.0f;
-                    }
-                }
-        }
-        if (!ok) {   // outside the table (within ~2 mm of the sub-element): Eq. 16 directly
-            if (HAS_Y) {   // both chains' Eq. 14 as packed pairs
-                const float2 kap2 = make_float2(P[0].kap, P[1].kap), y2 = make_float2(P[0].y, P[1].y);
-                const float2 ir2 = make_float2(P[0].inv_r, P[1].inv_r);
-#pragma unroll
-                for (int b = 0; b < NB; ++b) {
-                    float2 dr, di;
-                    delta_y2(gc, kap2, y2, ir2, qA + (float)b, dr, di);
-                    d[0][b] = make_float2(dr.x, di.x);
-                    d[1][b] = make_float2(dr.y, di.y);
-                }
-            } else {
-#pragma unroll
-                for (int c = 0; c < 2; ++c)
-#pragma unroll
-                    for (int b = 0; b < NB; ++b) d[c][b] = delta_f<HAS_Y>(gc, P[c], qA + (float)b);
-            }
-        }
-#pragma unroll
-        for (int b = 0; b < NB; ++b)
-#pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                o[c][b][0] += er[c][b] * d[c][b].x - ei[c][b] * d[c][b].y;
-                o[c][b][1] += er[c][b] * d[c][b].y + ei[c][b] * d[c][b].x;
-            }
-    }
-}
-
-// gen_two2 keeps the two element chains of gen_two in the .x and .y halves of packed
-// FP32 pairs (green.cuh).
 
 // Sub-element records of element pairs for gen_two2 (Y = 0): pair p = elements 2p, 2p + 1
 // (the last element repeated for odd N), sub-element mu at [2 (p nu + mu)], two float4 with
@@ -216,13 +78,27 @@ __device__ __forceinline__ float2 sinc_short2(float2 x) {
     return make_float2(sinc_short<0>(x.x), sinc_short<0>(x.y));
 }
 
-// gen_two at Y = 0 with the two chains as packed pairs: the same geometry (FP32 local
-// coordinates, one Newton step on r, exact double-float phase rate), phase seed and
-// phasor recurrence, sinc fit and delta table, each FP32 operation of both chains one
-// f32x2 instruction; the SFU operations, the table pieces (rows differ per chain) and the
-// range checks stay per chain.  sub: paired records (paired_sub).  QUAD: the table holds
-// quadratic pieces (the FP16 kernels), else cubic ones (split BF16).
-template <int NB, bool TAB, int SINC, bool LINEAR, bool QUAD>
+// Sub-element sums (Eq. 33) of the Green's terms of elements e0 and e0 + 1 for one
+// scatterer at the NB consecutive bins qA, qA + 1, ...: the two elements' evaluation chains
+// in the .x and .y halves of packed FP32 pairs (green.cuh), each FP32 operation of both
+// chains one f32x2 instruction, and one geometry setup per (scatterer, sub-element) for all
+// NB bins.  The SFU operations, the table pieces (rows differ per chain) and the range
+// checks stay per chain.  An element past N is evaluated on element N - 1 with zero
+// amplitude (no branch).
+// - Geometry in FP32 (local coordinates from the rotated centroid, r^2 with Y^2 where
+//   HAS_Y, one Newton step on r; absolute error ~ulp(0.1 m), relative error of r ~1e-7:
+//   a phase error below 3e-4 rad at the highest bin, under the 2^-11 rounding of the FP16
+//   operands) with the phase rate u = r df / c an exact double-float product: the phase is
+//   reduced exactly at bin qA, the later bins advance the phasor by one bin's phase and
+//   absorption.
+// - At Y = 0 with the table (TAB), bin qA picks the piece and the later bins reuse it: bin
+//   qA + b moves u by b kap/dx, small except within a few mm of the sub-element; up to half
+//   an interval outside the piece it is extrapolated, beyond that the bin takes its own
+//   piece, and outside the table delta is evaluated directly (Eq. 16).  QUAD: the table
+//   holds quadratic pieces (the FP16 kernels), else cubic ones (split BF16).
+// - HAS_Y: delta of Eq. 14 with the exponential factors (delta_y2), accumulated bin by bin.
+// sub: paired records (paired_sub).  (ore, oim)[b]: Re, Im of both elements at bin qA + b.
+template <int NB, bool TAB, int SINC, bool LINEAR, bool QUAD, bool HAS_Y>
 __device__ __forceinline__ void gen_two2(const GreenConst &gc, const float4 *sub,
                                          const float4 *tabs, const float4 &ps, int e0, float qA,
                                          float2 (&ore)[NB], float2 (&oim)[NB]) {
@@ -245,16 +121,19 @@ __device__ __forceinline__ void gen_two2(const GreenConst &gc, const float4 *sub
             lx = fma2(xs2, cp, fma2(dup2(-ps.z), sp, make_float2(B.x, B.y)));
             lz = fma2(xs2, sp, fma2(zs2, cp, make_float2(B.z, B.w)));
         }
-        float2 r2 = fma2(lx, lx, mul2(lz, lz));
+        float2 rho2 = fma2(lx, lx, mul2(lz, lz));
+        float2 r2 = HAS_Y ? add2(rho2, dup2(ps.y * ps.y)) : rho2;
         const bool v0 = r2.x > 1e-24f, v1 = r2.y > 1e-24f;   // a scatterer on a centroid is dropped
-        if (!v0) r2.x = 1.0f;
-        if (!v1) r2.y = 1.0f;
+        if (!v0) r2.x = rho2.x = 1.0f;
+        if (!v1) r2.y = rho2.y = 1.0f;
         const float2 rr = make_float2(rsqrt_a(r2.x), rsqrt_a(r2.y));
+        // the azimuth angle from the in-plane distance (Y != 0), else from r
+        const float2 irho = HAS_Y ? make_float2(rsqrt_a(rho2.x), rsqrt_a(rho2.y)) : rr;
         const float2 r0 = mul2(r2, rr);
         const float2 rh = fma2(fma2(neg2(r0), r0, r2), mul2(dup2(0.5f), rr), r0);
         const float2 uh = mul2(rh, dup2(gc.Kh));
         const float2 ul = fma2(rh, dup2(gc.Kl), fma2(rh, dup2(gc.Kh), neg2(uh)));
-        const float2 sin_t = mul2(lx, rr), cos_t = mul2(lz, rr);
+        const float2 sin_t = mul2(lx, irho), cos_t = mul2(lz, irho);
         float2 ob = gc.baffle == SIMUS_BAFFLE_SOFT ? cos_t
                   : (gc.baffle == SIMUS_BAFFLE_RIGID ? dup2(1.0f)
                      : make_float2(cos_t.x / (cos_t.x + gc.zeta), cos_t.y / (cos_t.y + gc.zeta)));
@@ -359,6 +238,17 @@ __device__ __forceinline__ void gen_two2(const GreenConst &gc, const float4 *sub
                     }
                 }
         }
+        if (HAS_Y) {   // Eq. 14 with the exponential factors, both chains as packed pairs,
+                       // accumulated bin by bin
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                float2 dre, dim;
+                delta_y2(gc, kap, dup2(ps.y), rr, qA + (float)b, dre, dim);
+                ore[b] = fma2(er[b], dre, fma2(neg2(ei[b]), dim, ore[b]));
+                oim[b] = fma2(er[b], dim, fma2(ei[b], dre, oim[b]));
+            }
+            continue;
+        }
         if (!ok) {   // outside the table (within ~2 mm of the sub-element): Eq. 16 directly
             PairSetup P;
 #pragma unroll
@@ -402,11 +292,9 @@ __device__ __forceinline__ void gen_tiles(const GreenConst &gc, const float4 *su
 #pragma unroll
         for (int jp = 0; jp < 4; ++jp) {
             float o[2][NB][2];
-            if (HAS_Y) {
-                gen_two<NB, TAB, HAS_Y, SINC, LINEAR>(gc, sub, tabs, ps, eg * 8 + 2 * jp, qA, o);
-            } else {
+            {
                 float2 ore[NB], oim[NB];
-                gen_two2<NB, TAB, SINC, LINEAR, !SPLIT>(gc, sub, tabs, ps, eg * 8 + 2 * jp, qA, ore, oim);
+                gen_two2<NB, TAB, SINC, LINEAR, !SPLIT, HAS_Y>(gc, sub, tabs, ps, eg * 8 + 2 * jp, qA, ore, oim);
 #pragma unroll
                 for (int b = 0; b < NB; ++b) {
                     o[0][b][0] = ore[b].x; o[1][b][0] = ore[b].y;
@@ -573,7 +461,7 @@ k_tc_rf(const TcUnit *__restrict__ units, int n_units, int64_t n_items, int *cou
         const uint32_t b1_part = (uint32_t)nN * K1 * 2, b2_part = (uint32_t)nN * 256 * 2;
         unsigned char *B2 = B1 + (size_t)nops * b1_part;
         float4 *sc = reinterpret_cast<float4 *>(B2 + (size_t)nops * b2_part);
-        float4 *sub = sc + kSB;        // compact records (Y != 0) or paired records (Y = 0)
+        float4 *sub = sc + kSB;        // paired sub-element records
         float4 *tabs = sub + M + gc.nu;                                    // delta table
         const bool use_tab = !HAS_Y && gc.tab_n > 0;
         const uint32_t abuf0 = tc::smem_u32(A0), abuf1 = tc::smem_u32(A1);
@@ -582,9 +470,7 @@ k_tc_rf(const TcUnit *__restrict__ units, int n_units, int64_t n_items, int *cou
         const uint32_t idesc2 = idesc1 | (1u << 15) | (1u << 16);   // A and B MN-major
         const uint32_t b1_bytes = nops * b1_part;
         if (ui != cur_unit) {
-            if (HAS_Y) {
-                for (int i = tid; i < M; i += kThreads) sub[i] = compact_sub(U.sub[i], LINEAR);
-            } else {
+            {
                 const int nu = gc.nu, np = ((N + 1) >> 1) * nu;
                 for (int i = tid; i < np; i += kThreads) {
                     const int pp = i / nu, mu = i - pp * nu;
